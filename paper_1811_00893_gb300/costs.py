@@ -1,0 +1,66 @@
+"""Per-site cost model: flops and algorithmic HBM bytes.
+
+Sec. 2, Table 1 counts, per lattice site of the Wilson matrix in single
+precision, 1368 flops and 1536 bytes moved with no cache reuse; with ideal
+reuse (each link used twice, each spinor nine times) the traffic drops to a
+byte/flop ratio of 0.351.  The functions below reproduce those figures and
+extend them to the even-odd hopping kernels this library runs, whose
+algorithmic bytes count every input spinor once, every link once per hopping
+application and every output once.
+"""
+from __future__ import annotations
+
+NC, NS = 3, 4
+SPINOR_REALS = 2 * NC * NS          # 24
+LINK_REALS = 2 * NC * NC            # 18
+HALF_SPINOR_REALS = SPINOR_REALS // 2
+
+# flops of one hopping application per output site: per direction a spin
+# projection (12), two SU(3) x colour-vector products (2 x 66) and the
+# accumulation into four spin components (24), less the first accumulation.
+FLOPS_PROJECT = 2 * NC * 2          # 6 complex adds = 12
+FLOPS_SU3_VEC = 9 * 6 + 6 * 2       # 9 complex mul + 6 complex add = 66
+FLOPS_HOP_SITE = 8 * (FLOPS_PROJECT + 2 * FLOPS_SU3_VEC + SPINOR_REALS) - SPINOR_REALS  # 1320
+FLOPS_D_SITE = FLOPS_HOP_SITE + 2 * SPINOR_REALS  # kappa * h and the subtraction: 1368
+
+
+def paper_bytes_per_site(word: int = 4, ideal_reuse: bool = False) -> int:
+    """Table 1's traffic per site of D: eight neighbour spinors, the site's own
+    spinor, eight links and the output (no reuse), or one spinor in, one out
+    and four links (ideal reuse: links twice, spinors nine times)."""
+    if ideal_reuse:
+        return word * (4 * LINK_REALS + 2 * SPINOR_REALS)
+    return word * (9 * SPINOR_REALS + 8 * LINK_REALS + SPINOR_REALS)
+
+
+def paper_byte_per_flop(ideal_reuse: bool = False) -> float:
+    return paper_bytes_per_site(4, ideal_reuse) / FLOPS_D_SITE
+
+
+def roofline_gflops(bandwidth_gbs: float, ideal_reuse: bool = False) -> float:
+    """Bandwidth-bound flop rate, as in Table 1's roofline columns."""
+    return bandwidth_gbs / paper_byte_per_flop(ideal_reuse)
+
+
+# ---- this library's kernels -------------------------------------------------
+
+#: bytes per real, per storage precision
+WORD = {"f64": 8, "f32": 4, "f16": 2}
+#: per-site norm bytes that ride along with an FP16 spinor
+NORM_BYTES = {"f64": 0, "f32": 0, "f16": 4}
+
+
+def spinor_bytes(prec: str) -> int:
+    return SPINOR_REALS * WORD[prec] + NORM_BYTES[prec]
+
+
+def link_bytes(prec: str) -> int:
+    return LINK_REALS * WORD[prec]
+
+
+def hop_bytes_per_site(prec: str, nrhs: int = 1, extra_in: int = 0, extra_out: int = 0) -> int:
+    """Algorithmic bytes per output site of one even-odd hopping kernel:
+    eight links read once for all right-hand sides, one input spinor and one
+    output spinor per right-hand side, plus `extra_in` / `extra_out` fused
+    epilogue fields per right-hand side."""
+    return 8 * link_bytes(prec) + nrhs * (1 + extra_in + 1 + extra_out) * spinor_bytes(prec)
