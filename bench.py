@@ -1,0 +1,457 @@
+#!/usr/bin/env python
+"""Benchmark of the Wilson-matrix solve on one GB300 (or N independent replicas).
+
+Default workload: a 32^3x64 lattice, even-odd preconditioned Wilson matrix,
+kappa = 0.124, smooth SU(3) links exp(i 0.3 A), one Gaussian source, solved to
+a true FP64 residual ||b - D x||/||b|| <= 1e-10 by FP32 BiCGStab with FP64
+defect correction.  One step = one complete solve through the C ABI
+(conversion of b, even-odd source, inner FP32 iterations with fused
+reductions, FP64 residual recomputations, reconstruction, final true
+residual, conversion of x).
+
+Reported:
+  value      whole-solve algorithmic HBM traffic / step time (GB/s), inputs
+             resident in device memory before the timed region;
+  e2e        the same with host (pinned) b and x: H2D and D2H inside each step;
+  roofline   the FP32 hopping kernel: its algorithmic bytes over its CUDA-event
+             time inside the timed region, against the measured HBM copy peak;
+  dslash     the paper's protocol (Sec. 5.4): 1000 back-to-back FP32 hopping
+             applications timed with CUDA events (GB/s, GFlop/s at 1320/site);
+  solve      mixed-precision vs plain FP64 BiCGStab time to 1e-10;
+  cpu_baseline  the FP64 CPU oracle on a bounded sample (BiCGStab iterations).
+
+`--impl reference` times the oracle itself on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Dslash GB/s & GFlop/s (% HBM peak); mixed vs FP64 solve time to 1e-10 residual"
+UNIT = "GB/s"
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD_INDEX = 1  # 32^3x64 even-odd, FP32 inner, FP64 defect correction
+PROFILE = os.path.join(ROOT, "profiles", "hop_f32_32x32x32x64.md")
+KERNEL_SOURCES = ["paper_1811_00893_gb300/csrc/dslash.cu", "paper_1811_00893_gb300/csrc/common.cuh"]
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle sample (for quick runs)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target duration of the oracle sample")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# process group
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world: int, backend: str):
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+
+
+def aggregate(local_bytes: float, local_ms: float, world: int, device="cpu"):
+    """Whole-job totals: bytes summed over ranks, time = max over ranks."""
+    if world <= 1:
+        return local_bytes, local_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_bytes], dtype=torch.float64, device=device)
+    m = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(t.item()), float(m.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_index],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index_for(local_rank: int) -> str:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+# ---------------------------------------------------------------------------
+# peaks and the committed ncu summary
+# ---------------------------------------------------------------------------
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the FP32 hopping kernel from the committed ncu
+    summary, or None when the kernel sources changed since it was taken."""
+    try:
+        with open(PROFILE) as f:
+            text = f.read()
+    except OSError:
+        return None
+    vals = {}
+    for ln in text.splitlines():
+        if ":" in ln and ln.lstrip().startswith("- "):
+            k, v = ln.lstrip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+
+def make_inputs(wl, rank: int, device: str):
+    from paper_1811_00893_gb300 import fields
+    U = fields.gauge_field(wl.dims, wl.links, wl.gauge_seed, device=device)
+    b = fields.gaussian_fermion(wl.dims, wl.nrhs, wl.source_seed + 100 * rank, device=device)
+    return U, b
+
+
+def config_of(wl):
+    return {"workload": f"{'x'.join(map(str, wl.dims))} Wilson even-odd, kappa={wl.kappa}, "
+                        f"{wl.links} links (eps=0.3), {wl.nrhs} Gaussian RHS; FP32 BiCGStab "
+                        f"+ FP64 defect correction to 1e-10 true residual",
+            "dims": list(wl.dims), "kappa": wl.kappa, "bc": "periodic xyz, antiperiodic t",
+            "nrhs": wl.nrhs, "tol": 1e-10, "inner": "f32", "outer": "f64",
+            "seeds": {"gauge": wl.gauge_seed, "source": wl.source_seed},
+            "l2": "inputs larger than L2 (FP32 links 604 MB, FP64 links 1208 MB per lattice)"}
+
+
+def oracle_sample(wl, U_host, b_host, seconds: float):
+    """Time the FP64 oracle's even-odd BiCGStab on this lattice for about
+    `seconds`; returns (GB/s of algorithmic traffic, cores, description)."""
+    import oracle
+    from paper_1811_00893_gb300 import costs
+    oracle.build()
+    be, bo = oracle.split(b_host, wl.dims)
+    bsys = be + wl.kappa * oracle.hop_eo(U_host, bo, wl.dims, wl.bc, 0)
+    t0 = time.perf_counter()
+    oracle.bicgstab_fixed(U_host, bsys, wl.dims, wl.bc, wl.kappa, True, 1)
+    t1 = time.perf_counter() - t0
+    n = int(max(1, min(60, seconds / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.bicgstab_fixed(U_host, bsys, wl.dims, wl.bc, wl.kappa, True, n)
+    dt = time.perf_counter() - t0
+    Vh = wl.volume // 2
+    per_iter = costs.bicgstab_iteration_bytes("f64", "f64") * Vh
+    return (n * per_iter / dt / 1e9, oracle.get_threads(),
+            f"{n} FP64 even-odd BiCGStab iterations of the oracle on the full "
+            f"{'x'.join(map(str, wl.dims))} lattice ({dt:.1f} s), bytes counted with the "
+            f"library's per-iteration model", dt / n)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_1811_00893_gb300 import costs, wilson
+    from paper_1811_00893_gb300.workloads import WORKLOADS
+
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = f"cuda:{local}"
+    wl = WORKLOADS[WORKLOAD_INDEX]
+    U, b = make_inputs(wl, rank, dev)
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    U_host = U.cpu().numpy() if want_cpu else None
+    b_host = b[0].cpu().numpy() if want_cpu else None
+    g = wilson.Gauge(wl.dims, wl.kappa, U, precs=("f64", "f32"), bc=wl.bc)
+    del U
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+    x = torch.zeros_like(b)
+    mixed = wilson.solve_params(tol=1e-10, eo=True, inner=wilson.WL_F32, graph_iters=0)
+
+    def solve(xx, bb, p=mixed):
+        return wilson.wilson_solve(g.handle, xx, bb, wl.nrhs, p)
+
+    for _ in range(max(3, args.warmup)):
+        rc, info = solve(x, b)
+    # ---------------- timed region: K solves, inputs resident in HBM
+    wilson.wl_timing(g.handle, True)
+    clk = ClockSampler(gpu_index_for(local)).start()
+    l0, b0 = wilson.wl_launch_count(), wilson.wl_algorithmic_bytes()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        rc, info = solve(x, b)
+        infos.append(info[0])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    ms_local = e0.elapsed_time(e1)
+    launches = wilson.wl_launch_count() - l0
+    bytes_local = wilson.wl_algorithmic_bytes() - b0
+    wilson.wl_timing(g.handle, False)
+    hop_ms, hop_n, hop_bytes = wilson.wl_timing_read(g.handle, wilson.WL_F32)
+    h64_ms, h64_n, h64_bytes = wilson.wl_timing_read(g.handle, wilson.WL_F64)
+    total_bytes, ms = aggregate(bytes_local, ms_local, world, device=dev)
+    ms_per_step = ms / args.steps
+    value = total_bytes / (ms / 1e3) / 1e9
+
+    # ---------------- e2e: host buffers through the same C call
+    b_h = b.cpu().pin_memory()
+    x_h = torch.zeros_like(b_h).pin_memory()
+    solve(x_h, b_h)
+    e2e_steps = max(1, args.steps // 2)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solve(x_h, b_h)
+    e2e_s = time.perf_counter() - t0
+    _, e2e_ms = aggregate(0.0, e2e_s * 1e3 / e2e_steps, world, device=dev)
+    step_bytes = total_bytes / args.steps
+    e2e_value = step_bytes / (e2e_ms / 1e3) / 1e9
+    nbytes_io = b.numel() * b.element_size()
+
+    # ---------------- the paper's mult protocol: 1000 back-to-back hops
+    fin = g.field("f32")
+    fout = g.field("f32")
+    wilson.wl_field_to_internal(g.handle, fin, b, 1, wilson.WL_F32, 1)
+    for _ in range(10):
+        wilson.wilson_dslash(g.handle, fout, fin, 0, 0, wilson.WL_F32, 1)
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    for _ in range(1000):
+        wilson.wilson_dslash(g.handle, fout, fin, 0, 0, wilson.WL_F32, 1)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    dslash_s = d0.elapsed_time(d1) / 1e3 / 1000
+    Vh = wl.volume // 2
+    peak, peak_kind = hbm_peak()
+    dslash_gbs = costs.hop_bytes_per_site("f32") * Vh / dslash_s / 1e9
+    dslash = {"gbs": dslash_gbs, "gflops": costs.FLOPS_HOP_SITE * Vh / dslash_s / 1e9,
+              "us_per_launch": dslash_s * 1e6, "frac_hbm": dslash_gbs / peak,
+              "bytes_per_site": costs.hop_bytes_per_site("f32"), "launches": 1000}
+
+    # ---------------- plain FP64 GPU solve for the time-to-solution comparison
+    x64 = torch.zeros_like(b)
+    p64 = wilson.solve_params(tol=1e-10, eo=True, inner=wilson.WL_F64, graph_iters=0)
+    solve(x64, b, p64)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    rc64, info64 = solve(x64, b, p64)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = f0.elapsed_time(f1)
+
+    out = None
+    if rank == 0:
+        achieved = hop_bytes / (hop_ms / 1e3) / 1e9 if hop_ms > 0 else None
+        traffic = profiled_traffic()
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "dtype_outer": "f64", "data": "synthetic",
+            "config": config_of(wl),
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes_io,
+                    "d2h_bytes_per_step": nbytes_io, "ms_per_step": e2e_ms,
+                    "timer": "wall clock around wilson_solve with pinned host b and x"},
+            "gpu_launches": launches,
+            "roofline": {"kernel": "hop_kernel<f32> (all hopping launches of the inner solve)",
+                         "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": traffic, "launches": hop_n,
+                         "algorithmic_bytes_per_launch": hop_bytes / max(hop_n, 1),
+                         "avg_us": hop_ms * 1e3 / max(hop_n, 1),
+                         "share_of_step": hop_ms / ms_local if ms_local else None,
+                         "f64_hop_share_of_step": h64_ms / ms_local if ms_local else None},
+            "dslash": dslash,
+            "solve": {"mixed_ms": ms_per_step, "fp64_ms": fp64_ms,
+                      "speedup_vs_fp64": fp64_ms / ms_per_step,
+                      "mixed_iters": infos[-1]["iters"], "mixed_outer": infos[-1]["outer"],
+                      "mixed_true_resid": max(i["true_resid"] for i in infos),
+                      "fp64_iters": info64[0]["iters"], "fp64_true_resid": info64[0]["true_resid"]},
+        }
+        if want_cpu:
+            gbs, cores, sample, s_per_iter = oracle_sample(wl, U_host, b_host, args.cpu_seconds)
+            out["cpu_baseline"] = {"value": gbs, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                   "sample": sample, "seconds_per_iteration": s_per_iter}
+        else:
+            out["cpu_baseline"] = None
+    g.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank, world, local):
+    if rank != 0:
+        return None
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1811_00893_gb300 import costs
+    from paper_1811_00893_gb300.workloads import WORKLOADS
+
+    wl = WORKLOADS[WORKLOAD_INDEX]
+    dev = f"cuda:{local}" if torch.cuda.is_available() else "cpu"
+    U, b = make_inputs(wl, 0, dev)  # same seeded inputs as the GPU arm
+    U_host, b_host = U.cpu().numpy(), b[0].cpu().numpy()
+    del U, b
+    oracle.build()
+    be, bo = oracle.split(b_host, wl.dims)
+    bsys = be + wl.kappa * oracle.hop_eo(U_host, bo, wl.dims, wl.bc, 0)
+    iters_per_step = 1
+    for _ in range(max(3, args.warmup)):
+        oracle.bicgstab_fixed(U_host, bsys, wl.dims, wl.bc, wl.kappa, True, iters_per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.bicgstab_fixed(U_host, bsys, wl.dims, wl.bc, wl.kappa, True, iters_per_step)
+    dt = time.perf_counter() - t0
+    Vh = wl.volume // 2
+    step_bytes = costs.bicgstab_iteration_bytes("f64", "f64") * Vh * iters_per_step
+    value = step_bytes * args.steps / dt / 1e9
+    sample = (f"each step: {iters_per_step} FP64 even-odd BiCGStab iteration of the oracle on the "
+              f"full {'x'.join(map(str, wl.dims))} lattice from x = 0")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(wl),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(),
+                             "kind": "oracle", "sample": sample}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world, local)
+    else:
+        out = run_ours(args, rank, world, local)
+    if out is not None and rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

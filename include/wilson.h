@@ -1,0 +1,198 @@
+/*
+ * wilson.h -- C ABI of the GB300 Wilson-matrix library.
+ *
+ * The library applies the Wilson fermion matrix of lattice QCD,
+ *     D(x,y) = delta_{x,y} - kappa * sum_mu [ (1 - gamma_mu) U_mu(x) delta_{x+mu,y}
+ *                                           + (1 + gamma_mu) U_mu(x-mu)^dag delta_{x-mu,y} ]
+ * (Eq. 1, Sec. 2 "Wilson Fermion Matrix"), and solves D x = b with BiCGStab
+ * (Sec. 2, the paragraph after Table 1), in FP64, FP32 and FP16 storage, with
+ * FP64 defect correction or reliable updates (the "mixed precision solver"
+ * that the same paragraph names), for many right-hand sides at once.
+ *
+ * Conventions
+ *   Lattice   extents Lx, Ly, Lz, Lt, all even and >= 2; site index
+ *             s = x + Lx*(y + Ly*(z + Lz*t)) (x fastest, as in Sec. 4.1).
+ *             V = Lx*Ly*Lz*Lt, Vh = V/2.  Parity of a site = (x+y+z+t) mod 2;
+ *             the half index of site s is s/2.
+ *   Gamma     the paper fixes no basis; the library uses the Hermitian chiral
+ *             (DeGrand-Rossi) basis, gamma_5 = diag(1, 1, -1, -1).
+ *   Boundary  Sec. 2 allows periodic or antiperiodic conditions.  A hop across
+ *             the lattice edge in direction mu is multiplied by the unit phase
+ *             phi_mu (forward) or conj(phi_mu) (backward).
+ *   Canonical FP64 layouts (what callers hand in):
+ *             gauge field  U[V][4][3][3] complex double (re, im interleaved)
+ *             fermion      psi[nrhs][V][4][3] complex double (spin, colour)
+ *   Internal  half-lattice fields in the library's own structure-of-arrays
+ *             layout (one per parity and right-hand side); their size comes
+ *             from wl_field_bytes() and they are produced and read back with
+ *             wl_field_to_internal() / wl_field_to_canonical().
+ *
+ * Ownership and streams
+ *   The caller owns every field buffer (x, b, in, out) and the CUDA stream;
+ *   `stream` is a cudaStream_t (NULL = legacy default stream).  A wl_gauge
+ *   owns its internal link copies and solver workspace and frees them in
+ *   wl_gauge_destroy().  All calls except the solves are asynchronous on
+ *   `stream`; the solves synchronise `stream` before returning.
+ *
+ * Errors
+ *   Every call returns 0 (WL_OK) or a negative WL_ERR_* code; the message of
+ *   the last error on the calling thread is returned by wl_last_error().
+ *   Arguments are validated on the host before any launch.
+ */
+#ifndef WILSON_H
+#define WILSON_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { WL_F64 = 0, WL_F32 = 1, WL_F16 = 2 } wl_prec;
+
+#define WL_PREC_MASK(p) (1 << (p))
+#define WL_PREC_ALL 7
+
+enum {
+    WL_OK = 0,
+    WL_ERR_ARG = -1,            /* invalid argument (message says which) */
+    WL_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+    WL_ERR_NOT_CONVERGED = -3,  /* maxiter reached; x holds the best iterate */
+    WL_ERR_BREAKDOWN = -4,      /* BiCGStab broke down more often than it may restart */
+    WL_ERR_NAN = -5,            /* a reduction produced NaN or Inf */
+    WL_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up */
+    WL_ERR_STATE = -7           /* the gauge object lacks what the call needs */
+};
+
+typedef struct {
+    int dims[4];       /* Lx, Ly, Lz, Lt: even, >= 2 */
+    double kappa;      /* hopping parameter, kappa = 1/(8 + 2 m0) (Eq. 1); |kappa| < 1/8
+                          guarantees that D is invertible */
+    double bc_re[4];   /* boundary phase phi_mu = bc_re + i bc_im per direction, |phi| = 1 */
+    double bc_im[4];
+} wl_lattice;
+
+typedef struct wl_gauge_s* wl_gauge;
+
+/* Create a gauge object from the canonical FP64 gauge field U (device memory,
+ * V*4*9 complex, Sec. 2 "link variable").  prec_mask selects which internal
+ * link copies to build (WL_PREC_MASK(WL_F32) | ...); FP64 links are always
+ * built because the outer residual of every solve is FP64.  Returns
+ * WL_ERR_ARG for odd or small extents, |phi| != 1 or a NULL pointer.  U is
+ * only read during the call (stream-ordered) and may be freed afterwards. */
+int wl_gauge_create(wl_gauge* g, const wl_lattice* lat, const double* U, int prec_mask,
+                    void* stream);
+int wl_gauge_destroy(wl_gauge g);
+
+/* Vh of the gauge object's lattice. */
+long long wl_half_volume(wl_gauge g);
+
+/* Bytes of `nrhs` internal half-lattice fields of precision `prec`, stored
+ * back to back (right-hand side r starts at r * wl_field_bytes(g, prec, 1)).
+ * A full-lattice internal field is two half fields, even then odd. */
+size_t wl_field_bytes(wl_gauge g, wl_prec prec, int nrhs);
+
+/* Copy the parity-`parity` sites of nrhs canonical FP64 fields `in` (device,
+ * nrhs*V*12 complex) into internal half fields `out` of precision `prec`
+ * (FP16 stores each site scaled by its largest |real component|, kept as a
+ * per-site FP32 norm).  Asynchronous. */
+int wl_field_to_internal(wl_gauge g, void* out, const double* in, int parity, wl_prec prec,
+                         int nrhs, void* stream);
+
+/* Inverse of wl_field_to_internal: write the parity-`parity` sites of the
+ * canonical fields `out`; the other parity's sites are left untouched. */
+int wl_field_to_canonical(wl_gauge g, double* out, const void* in, int parity, wl_prec prec,
+                          int nrhs, void* stream);
+
+/* Hopping term (the Dslash) between checkerboards, Eq. 1's bracketed sum:
+ *     out_p = H_{p,1-p} in_{1-p},   p = out_parity,
+ * for nrhs right-hand sides (half fields back to back).  dagger = 1 applies
+ * the hopping term of D^dag (gamma_mu -> -gamma_mu).  No kappa.  `out` and
+ * `in` must not overlap.  Flop count: 1320 per output site per right-hand
+ * side. */
+int wilson_dslash(wl_gauge g, void* out, const void* in, int out_parity, int dagger,
+                  wl_prec prec, int nrhs, void* stream);
+
+/* Matrix apply:
+ *   eo = 0: out = D in on full-lattice internal fields (Eq. 1; 1368 flop/site);
+ *   eo = 1: out = M_ee in = in - kappa^2 H_eo H_oe in on even half fields
+ *           (the Schur complement of D on the even sites).
+ * dagger = 1 applies D^dag / M_ee^dag.  `out` and `in` must not overlap.
+ * eo = 1 uses an odd-parity temporary from the gauge object's workspace. */
+int wilson_mult(wl_gauge g, void* out, const void* in, int eo, int dagger, wl_prec prec,
+                int nrhs, void* stream);
+
+/* Per-right-hand-side complex dot products and norms of internal half
+ * fields (the global reductions of BiCGStab, Sec. 2):
+ *     out[3r+0] + i out[3r+1] = sum conj(a_r) b_r,   out[3r+2] = ||b_r||^2.
+ * `out` is device memory (3*nrhs doubles); accumulation is FP64 from the
+ * warp level up.  Uses partial sums in the gauge object's workspace. */
+int wl_cdot(wl_gauge g, double* out, const void* a, const void* b, wl_prec prec, int nrhs,
+            void* stream);
+
+typedef struct {
+    double tol;        /* stop when ||b - D x||_2 / ||b||_2 <= tol (full D, FP64), per RHS */
+    int maxiter;       /* bound on inner iterations, per RHS */
+    int eo;            /* 1: solve the even-odd Schur system M_ee x_e = b_e + kappa H_eo b_o */
+    wl_prec inner;     /* precision of the Krylov iteration; WL_F64 = plain FP64 BiCGStab */
+    double inner_tol;  /* defect correction: relative tolerance of each inner solve (0: default) */
+    double delta;      /* > 0: reliable updates (recompute the FP64 residual when the iterated
+                          residual drops below delta times its maximum since the last update)
+                          instead of restarted defect correction */
+    int use_x0;        /* 1: x holds the initial guess */
+    int graph_iters;   /* > 0: capture this many iterations per CUDA-graph replay (the host
+                          checks convergence after each replay); <= 0: eager launches with
+                          a host check every max(1, -graph_iters) iterations (4 when 0) */
+} wl_solve_params;
+
+typedef struct {
+    int iters;          /* inner iterations */
+    int outer;          /* FP64 residual recomputations (defect corrections / reliable updates) */
+    int restarts;       /* breakdown restarts */
+    int status;         /* WL_OK or WL_ERR_* for this right-hand side */
+    double true_resid;  /* final ||b - D x|| / ||b||, FP64 on the GPU */
+    double secs;        /* wall time of the whole call */
+} wl_solve_info;
+
+/* Solve D x_r = b_r for nrhs right-hand sides (canonical FP64, nrhs*V*12
+ * complex each).  x and b may be device or host memory (host buffers are
+ * staged through the gauge object's workspace).  info has nrhs entries.
+ * Returns WL_OK when every right-hand side reached tol, else the first
+ * failing status; x always holds the best iterate. */
+int wilson_solve(wl_gauge g, double* x, const double* b, int nrhs, const wl_solve_params* p,
+                 wl_solve_info* info, void* stream);
+
+/* Solve nlat independent systems of different lattices together: gauge
+ * object gs[l] with nrhs[l] right-hand sides x[l], b[l] (device, canonical).
+ * Hopping and vector kernels run as single persistent launches over all
+ * lattices.  info receives sum(nrhs) entries, lattice by lattice. */
+int wilson_solve_batch(int nlat, const wl_gauge* gs, double* const* x, const double* const* b,
+                       const int* nrhs, const wl_solve_params* p, wl_solve_info* info,
+                       void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* wl_last_error(void);
+
+/* Kernels the library has launched so far in this process (a CUDA-graph
+ * replay counts every kernel node it runs). */
+long long wl_launch_count(void);
+
+/* Algorithmic bytes of those launches: each kernel counts the fields it must
+ * read and write once (links once per hopping launch for all right-hand
+ * sides, every spinor operand once), not the traffic the hardware saw. */
+double wl_algorithmic_bytes(void);
+
+/* Per-launch CUDA-event timing of the hopping kernels launched by this gauge
+ * object (eager launches only; launches inside graph capture are not timed):
+ * enable = 1 clears and starts recording, enable = 0 stops.  wl_timing_read
+ * returns, for hopping launches of precision `prec` (-1: all), the summed
+ * kernel time in ms, the number of timed launches and their summed
+ * algorithmic bytes.  It waits for the recorded events. */
+int wl_timing(wl_gauge g, int enable);
+int wl_timing_read(wl_gauge g, int prec, double* ms, long long* launches, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WILSON_H */

@@ -64,3 +64,19 @@ def hop_bytes_per_site(prec: str, nrhs: int = 1, extra_in: int = 0, extra_out: i
     output spinor per right-hand side, plus `extra_in` / `extra_out` fused
     epilogue fields per right-hand side."""
     return 8 * link_bytes(prec) + nrhs * (1 + extra_in + 1 + extra_out) * spinor_bytes(prec)
+
+
+def bicgstab_iteration_bytes(prec: str, xprec: str, eo: bool = True) -> int:
+    """Algorithmic bytes per site of one BiCGStab iteration as this library
+    schedules it (per half-lattice site for eo, per lattice site for the full
+    D).  Matrix applies: M_ee is two hopping launches, the first writing an
+    odd temporary (links, in, out) and the second fusing the xpay and the dot
+    (links, in, out, x1, w); the full D is one launch per apply that fuses
+    both (links, in, out, x1, w).  Vector passes: p update 4 fields, s update
+    3, x/r update 5 plus reading and writing x."""
+    sp, lk, xb = spinor_bytes(prec), 8 * link_bytes(prec), spinor_bytes(xprec)
+    if eo:
+        applies = 2 * ((lk + 2 * sp) + (lk + 4 * sp))
+    else:
+        applies = 2 * (lk + 4 * sp)
+    return applies + (4 + 3 + 5) * sp + 2 * xb

@@ -1,0 +1,439 @@
+// Gauge objects: validation, the internal link layouts, layout conversion of
+// fermion fields, workspace growth and per-launch timing.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace wl {
+
+std::atomic<long long> g_launches{0};
+std::atomic<long long> g_bytes{0};
+
+static thread_local std::string t_last_error;
+
+int set_error(int code, const std::string& msg)
+{
+    t_last_error = msg;
+    return code;
+}
+
+Geom make_geom(const int* dims)
+{
+    Geom g;
+    for (int k = 0; k < 4; ++k) g.L[k] = dims[k];
+    g.Lxh = dims[0] / 2;
+    g.Vh = (long long)dims[0] * dims[1] * dims[2] * dims[3] / 2;
+    g.sy = g.Lxh;
+    g.sz = g.sy * dims[1];
+    g.st = g.sz * dims[2];
+    return g;
+}
+
+bool is_capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st != cudaStreamCaptureStatusNone;
+}
+
+// Canonical site index of half index i on parity p.
+__device__ __forceinline__ long long site_of_half(const Geom& g, int p, long long i)
+{
+    const long long row = i / g.Lxh;  // (y, z, t) row
+    const int y = (int)(row % g.L[1]);
+    const int z = (int)((row / g.L[1]) % g.L[2]);
+    const int t = (int)(row / ((long long)g.L[1] * g.L[2]));
+    return 2 * i + ((p + y + z + t) & 1);
+}
+
+// ---------------------------------------------------------------------------
+// links: W_d(x) for the 8 hops of each output site, phases folded in,
+// backward links daggered.
+// ---------------------------------------------------------------------------
+
+template <int P>
+__device__ __forceinline__ void store_link(void* base, long long Vh, int d, long long i,
+                                           const cx<double> (&w)[9]);
+
+template <>
+__device__ __forceinline__ void store_link<WL_F64>(void* base, long long Vh, int d, long long i,
+                                                   const cx<double> (&w)[9])
+{
+    double2* p = (double2*)base + (long long)d * 9 * Vh;
+    for (int k = 0; k < 9; ++k) p[k * Vh + i] = make_double2(w[k].re, w[k].im);
+}
+template <>
+__device__ __forceinline__ void store_link<WL_F32>(void* base, long long Vh, int d, long long i,
+                                                   const cx<double> (&w)[9])
+{
+    float4* p = (float4*)base + (long long)d * 4 * Vh;
+    for (int k = 0; k < 4; ++k)
+        p[k * Vh + i] = make_float4((float)w[2 * k].re, (float)w[2 * k].im, (float)w[2 * k + 1].re,
+                                    (float)w[2 * k + 1].im);
+    float2* q = (float2*)((float4*)base + 8 * 4 * Vh) + (long long)d * Vh;
+    q[i] = make_float2((float)w[8].re, (float)w[8].im);
+}
+template <>
+__device__ __forceinline__ void store_link<WL_F16>(void* base, long long Vh, int d, long long i,
+                                                   const cx<double> (&w)[9])
+{
+    // |entries| <= 1 for unitary links, so FP16 needs no scale
+    uint4* p = (uint4*)base + (long long)d * 2 * Vh;
+    for (int k = 0; k < 2; ++k) {
+        uint4 t;
+        t.x = f2h((float)w[4 * k].re, (float)w[4 * k].im);
+        t.y = f2h((float)w[4 * k + 1].re, (float)w[4 * k + 1].im);
+        t.z = f2h((float)w[4 * k + 2].re, (float)w[4 * k + 2].im);
+        t.w = f2h((float)w[4 * k + 3].re, (float)w[4 * k + 3].im);
+        p[k * Vh + i] = t;
+    }
+    unsigned* q = (unsigned*)((uint4*)base + 8 * 2 * Vh) + (long long)d * Vh;
+    q[i] = f2h((float)w[8].re, (float)w[8].im);
+}
+
+struct BC {
+    double re[4], im[4];
+};
+
+template <int P>
+__global__ void build_links_kernel(void* out, const double* __restrict__ U, Geom g, BC bc, int p)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.Vh) return;
+    const long long s = site_of_half(g, p, i);
+    int c[4];
+    long long r = s;
+    for (int mu = 0; mu < 4; ++mu) {
+        c[mu] = (int)(r % g.L[mu]);
+        r /= g.L[mu];
+    }
+    const long long stride[4] = {1, g.L[0], (long long)g.L[0] * g.L[1],
+                                 (long long)g.L[0] * g.L[1] * g.L[2]};
+    for (int mu = 0; mu < 4; ++mu) {
+        cx<double> w[9];
+        // forward: phi^[x_mu = L-1] U_mu(x)
+        const double* u = U + (s * 4 + mu) * 18;
+        double pr = 1.0, pi = 0.0;
+        if (c[mu] == g.L[mu] - 1) { pr = bc.re[mu]; pi = bc.im[mu]; }
+        for (int k = 0; k < 9; ++k) {
+            const double a = u[2 * k], b = u[2 * k + 1];
+            w[k] = {pr * a - pi * b, pr * b + pi * a};
+        }
+        store_link<P>(out, g.Vh, 2 * mu, i, w);
+        // backward: conj(phi)^[x_mu = 0] U_mu(x - mu)^dag
+        const long long n = (c[mu] == 0) ? s + (g.L[mu] - 1) * stride[mu] : s - stride[mu];
+        const double* v = U + (n * 4 + mu) * 18;
+        pr = 1.0;
+        pi = 0.0;
+        if (c[mu] == 0) { pr = bc.re[mu]; pi = -bc.im[mu]; }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                const double re = v[2 * (b * 3 + a)], im = -v[2 * (b * 3 + a) + 1];
+                w[a * 3 + b] = {pr * re - pi * im, pr * im + pi * re};
+            }
+        store_link<P>(out, g.Vh, 2 * mu + 1, i, w);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fermion layout conversion
+// ---------------------------------------------------------------------------
+
+template <int P>
+__global__ void to_internal_kernel(char* out, const double* __restrict__ in, Geom g, int p,
+                                   size_t fb, long long V)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int rhs = blockIdx.y;
+    if (i >= g.Vh) return;
+    const long long s = site_of_half(g, p, i);
+    const double* q = in + ((long long)rhs * V + s) * 24;
+    cx<typename Prec<P>::real> v[12];
+    for (int c = 0; c < 12; ++c)
+        v[c] = {(typename Prec<P>::real)q[2 * c], (typename Prec<P>::real)q[2 * c + 1]};
+    store_spinor<P>(out + rhs * fb, g.Vh, i, v);
+}
+
+template <int P>
+__global__ void to_canonical_kernel(double* out, const char* in, Geom g, int p, size_t fb,
+                                    long long V)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int rhs = blockIdx.y;
+    if (i >= g.Vh) return;
+    const long long s = site_of_half(g, p, i);
+    double* q = out + ((long long)rhs * V + s) * 24;
+    cx<typename Prec<P>::real> v[12];
+    load_spinor<P>(v, in + rhs * fb, g.Vh, i);
+    for (int c = 0; c < 12; ++c) {
+        q[2 * c] = (double)v[c].re;
+        q[2 * c + 1] = (double)v[c].im;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// workspace growth
+// ---------------------------------------------------------------------------
+
+int ensure_red(wl_gauge g, int slots, long long blocks)
+{
+    if (slots <= g->red_slots && blocks <= g->red.max_blocks) return WL_OK;
+    const int ns = slots > g->red_slots ? slots : g->red_slots;
+    const long long nb = blocks > g->red.max_blocks ? blocks : g->red.max_blocks;
+    WL_CUDA(cudaDeviceSynchronize());
+    if (g->red.partial) cudaFree(g->red.partial);
+    if (g->red.ticket) cudaFree(g->red.ticket);
+    g->red.partial = nullptr;
+    g->red.ticket = nullptr;
+    WL_CUDA(cudaMalloc(&g->red.partial, sizeof(double) * 4 * (size_t)ns * (size_t)nb));
+    WL_CUDA(cudaMalloc(&g->red.ticket, sizeof(unsigned) * (size_t)ns));
+    WL_CUDA(cudaMemset(g->red.ticket, 0, sizeof(unsigned) * (size_t)ns));
+    g->red.max_blocks = (int)nb;
+    g->red_slots = ns;
+    g->red_gen++;
+    return WL_OK;
+}
+
+int ensure_tmp(wl_gauge g, int prec, size_t bytes)
+{
+    if (g->tmp_bytes[prec] >= bytes) return WL_OK;
+    WL_CUDA(cudaDeviceSynchronize());
+    if (g->tmp[prec]) cudaFree(g->tmp[prec]);
+    g->tmp[prec] = nullptr;
+    WL_CUDA(cudaMalloc(&g->tmp[prec], bytes));
+    g->tmp_bytes[prec] = bytes;
+    return WL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// timing
+// ---------------------------------------------------------------------------
+
+static const size_t kTimingPool = 1 << 14;
+
+void timing_begin(wl_gauge g, cudaStream_t s, double bytes, int prec, int* slot)
+{
+    *slot = -1;
+    Timing& t = g->timing;
+    if (!t.on) return;
+    if (is_capturing(s) || t.used >= t.start.size()) {
+        t.dropped++;
+        return;
+    }
+    *slot = (int)t.used++;
+    t.bytes[*slot] = bytes;
+    t.prec[*slot] = prec;
+    cudaEventRecord(t.start[*slot], s);
+}
+
+void timing_end(wl_gauge g, cudaStream_t s, int slot)
+{
+    if (slot >= 0) cudaEventRecord(g->timing.stop[slot], s);
+}
+
+}  // namespace wl
+
+using namespace wl;
+
+static int validate_lattice(const wl_lattice* lat)
+{
+    if (!lat) return set_error(WL_ERR_ARG, "NULL lattice");
+    long long V = 1;
+    for (int k = 0; k < 4; ++k) {
+        if (lat->dims[k] < 2 || lat->dims[k] % 2)
+            return set_error(WL_ERR_ARG, "lattice extents must be even and >= 2");
+        V *= lat->dims[k];
+    }
+    if (V / 2 > 0x7fffffffLL / 16)
+        return set_error(WL_ERR_ARG, "lattice too large for 32-bit half-index arithmetic");
+    for (int k = 0; k < 4; ++k) {
+        const double m = std::hypot(lat->bc_re[k], lat->bc_im[k]);
+        if (std::fabs(m - 1.0) > 1e-12) return set_error(WL_ERR_ARG, "boundary phases must have |phi| = 1");
+    }
+    if (!std::isfinite(lat->kappa)) return set_error(WL_ERR_ARG, "kappa must be finite");
+    return WL_OK;
+}
+
+extern "C" int wl_gauge_create(wl_gauge* out, const wl_lattice* lat, const double* U, int prec_mask,
+                               void* stream)
+{
+    if (!out) return set_error(WL_ERR_ARG, "NULL output handle");
+    *out = nullptr;
+    WL_TRY(validate_lattice(lat));
+    if (!U) return set_error(WL_ERR_ARG, "NULL gauge field");
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, U) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return set_error(WL_ERR_ARG, "gauge field must be device memory");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    auto g = new wl_gauge_s();
+    g->geo = make_geom(lat->dims);
+    g->kappa = lat->kappa;
+    for (int k = 0; k < 4; ++k) {
+        g->bc_re[k] = lat->bc_re[k];
+        g->bc_im[k] = lat->bc_im[k];
+    }
+    g->prec_mask = (prec_mask & WL_PREC_ALL) | WL_PREC_MASK(WL_F64);
+    int rc = WL_OK;
+    do {
+        if (cudaGetDevice(&g->device) != cudaSuccess) { rc = set_error(WL_ERR_CUDA, "cudaGetDevice"); break; }
+        cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+        BC bc;
+        for (int k = 0; k < 4; ++k) {
+            bc.re[k] = lat->bc_re[k];
+            bc.im[k] = lat->bc_im[k];
+        }
+        const int block = 128;
+        const unsigned grid = (unsigned)((g->geo.Vh + block - 1) / block);
+        for (int prec = 0; prec < 3 && rc == WL_OK; ++prec) {
+            if (!(g->prec_mask & WL_PREC_MASK(prec))) continue;
+            for (int p = 0; p < 2; ++p) {
+                cudaError_t e = cudaMalloc(&g->links[prec][p], link_field_bytes(prec, g->geo.Vh));
+                if (e != cudaSuccess) {
+                    rc = set_error(WL_ERR_CUDA, std::string("cudaMalloc links: ") + cudaGetErrorString(e));
+                    break;
+                }
+                if (prec == WL_F64) build_links_kernel<WL_F64><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, bc, p);
+                else if (prec == WL_F32) build_links_kernel<WL_F32><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, bc, p);
+                else build_links_kernel<WL_F16><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, bc, p);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) {
+                    rc = set_error(WL_ERR_CUDA, std::string("link build launch: ") + cudaGetErrorString(e));
+                    break;
+                }
+                count_launch(1, (double)g->geo.Vh * (8 * 144.0 + link_field_bytes(prec, 1)));
+            }
+        }
+        if (rc != WL_OK) break;
+        // the link build reads U: finish before returning so U may be freed
+        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(WL_ERR_CUDA, "link build failed"); break; }
+    } while (0);
+    if (rc != WL_OK) {
+        wl_gauge_destroy(g);
+        return rc;
+    }
+    *out = g;
+    return WL_OK;
+}
+
+void free_workspace(wl_gauge g);  // solver.cu
+
+extern "C" int wl_gauge_destroy(wl_gauge g)
+{
+    if (!g) return WL_OK;
+    cudaDeviceSynchronize();
+    free_workspace(g);
+    for (int prec = 0; prec < 3; ++prec) {
+        for (int p = 0; p < 2; ++p)
+            if (g->links[prec][p]) cudaFree(g->links[prec][p]);
+        if (g->tmp[prec]) cudaFree(g->tmp[prec]);
+    }
+    if (g->red.partial) cudaFree(g->red.partial);
+    if (g->red.ticket) cudaFree(g->red.ticket);
+    for (auto e : g->timing.start) cudaEventDestroy(e);
+    for (auto e : g->timing.stop) cudaEventDestroy(e);
+    delete g;
+    return WL_OK;
+}
+
+extern "C" long long wl_half_volume(wl_gauge g) { return g ? g->geo.Vh : 0; }
+
+extern "C" size_t wl_field_bytes(wl_gauge g, wl_prec prec, int nrhs)
+{
+    if (!g || prec < WL_F64 || prec > WL_F16 || nrhs < 0) return 0;
+    return spinor_field_bytes(prec, g->geo.Vh) * (size_t)nrhs;
+}
+
+static int conv_check(wl_gauge g, const void* a, const void* b, int parity, wl_prec prec, int nrhs)
+{
+    if (!g) return set_error(WL_ERR_ARG, "NULL gauge object");
+    if (!a || !b) return set_error(WL_ERR_ARG, "NULL field pointer");
+    if (parity != 0 && parity != 1) return set_error(WL_ERR_ARG, "parity must be 0 or 1");
+    if (prec < WL_F64 || prec > WL_F16) return set_error(WL_ERR_ARG, "unknown precision");
+    if (nrhs < 1 || nrhs > 65535) return set_error(WL_ERR_ARG, "nrhs must be in 1..65535");
+    return WL_OK;
+}
+
+extern "C" int wl_field_to_internal(wl_gauge g, void* out, const double* in, int parity, wl_prec prec,
+                                    int nrhs, void* stream)
+{
+    WL_TRY(conv_check(g, out, in, parity, prec, nrhs));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int block = 128;
+    dim3 grid((unsigned)((g->geo.Vh + block - 1) / block), (unsigned)nrhs);
+    const size_t fb = spinor_field_bytes(prec, g->geo.Vh);
+    const long long V = 2 * g->geo.Vh;
+    if (prec == WL_F64) to_internal_kernel<WL_F64><<<grid, block, 0, s>>>((char*)out, in, g->geo, parity, fb, V);
+    else if (prec == WL_F32) to_internal_kernel<WL_F32><<<grid, block, 0, s>>>((char*)out, in, g->geo, parity, fb, V);
+    else to_internal_kernel<WL_F16><<<grid, block, 0, s>>>((char*)out, in, g->geo, parity, fb, V);
+    WL_CHECK_LAUNCH((double)nrhs * g->geo.Vh * (192.0 + (double)fb / g->geo.Vh));
+    return WL_OK;
+}
+
+extern "C" int wl_field_to_canonical(wl_gauge g, double* out, const void* in, int parity, wl_prec prec,
+                                     int nrhs, void* stream)
+{
+    WL_TRY(conv_check(g, out, in, parity, prec, nrhs));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int block = 128;
+    dim3 grid((unsigned)((g->geo.Vh + block - 1) / block), (unsigned)nrhs);
+    const size_t fb = spinor_field_bytes(prec, g->geo.Vh);
+    const long long V = 2 * g->geo.Vh;
+    if (prec == WL_F64) to_canonical_kernel<WL_F64><<<grid, block, 0, s>>>(out, (const char*)in, g->geo, parity, fb, V);
+    else if (prec == WL_F32) to_canonical_kernel<WL_F32><<<grid, block, 0, s>>>(out, (const char*)in, g->geo, parity, fb, V);
+    else to_canonical_kernel<WL_F16><<<grid, block, 0, s>>>(out, (const char*)in, g->geo, parity, fb, V);
+    WL_CHECK_LAUNCH((double)nrhs * g->geo.Vh * (192.0 + (double)fb / g->geo.Vh));
+    return WL_OK;
+}
+
+extern "C" const char* wl_last_error(void) { return wl::t_last_error.c_str(); }
+
+extern "C" long long wl_launch_count(void) { return wl::g_launches.load(); }
+
+extern "C" double wl_algorithmic_bytes(void) { return (double)wl::g_bytes.load(); }
+
+extern "C" int wl_timing(wl_gauge g, int enable)
+{
+    if (!g) return set_error(WL_ERR_ARG, "NULL gauge object");
+    Timing& t = g->timing;
+    if (enable) {
+        if (t.start.empty()) {
+            t.start.resize(kTimingPool);
+            t.stop.resize(kTimingPool);
+            t.bytes.resize(kTimingPool);
+            t.prec.resize(kTimingPool);
+            for (size_t k = 0; k < kTimingPool; ++k) {
+                WL_CUDA(cudaEventCreate(&t.start[k]));
+                WL_CUDA(cudaEventCreate(&t.stop[k]));
+            }
+        }
+        t.used = 0;
+        t.dropped = 0;
+    }
+    t.on = enable != 0;
+    return WL_OK;
+}
+
+extern "C" int wl_timing_read(wl_gauge g, int prec, double* ms, long long* launches, double* bytes)
+{
+    if (!g) return set_error(WL_ERR_ARG, "NULL gauge object");
+    Timing& t = g->timing;
+    double total = 0.0, b = 0.0;
+    long long n = 0;
+    for (size_t k = 0; k < t.used; ++k) {
+        if (prec >= 0 && t.prec[k] != prec) continue;
+        ++n;
+        WL_CUDA(cudaEventSynchronize(t.stop[k]));
+        float e = 0.f;
+        WL_CUDA(cudaEventElapsedTime(&e, t.start[k], t.stop[k]));
+        total += e;
+        b += t.bytes[k];
+    }
+    if (ms) *ms = total;
+    if (launches) *launches = n;
+    if (bytes) *bytes = b;
+    return WL_OK;
+}

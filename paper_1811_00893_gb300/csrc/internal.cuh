@@ -1,0 +1,114 @@
+// Host-side internals shared by the library's translation units: the gauge
+// object, lattice geometry, kernel-launch helpers and solver workspace.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace wl {
+
+// Lattice geometry in half-lattice (checkerboard) index units.
+struct Geom {
+    int L[4];      // Lx, Ly, Lz, Lt
+    int Lxh;       // Lx / 2
+    long long Vh;  // half volume
+    long long sy, sz, st;  // half-index strides of y, z, t
+};
+
+// Per-launch event timing of hopping kernels (see wl_timing).
+struct Timing {
+    bool on = false;
+    std::vector<cudaEvent_t> start, stop;
+    std::vector<double> bytes;
+    std::vector<int> prec;
+    size_t used = 0;
+    long long dropped = 0;
+};
+
+struct Workspace;  // solver.cu
+
+// Tuned launch shape of one kernel configuration (autotuner cache entry).
+struct Tuned {
+    int block = 0;     // threads per block
+    int rhs_tile = 1;  // right-hand sides per thread block (multi-RHS hop)
+};
+
+}  // namespace wl
+
+struct wl_gauge_s {
+    wl::Geom geo;
+    double kappa;
+    double bc_re[4], bc_im[4];
+    int prec_mask;
+    int device;
+    int num_sms;
+    void* links[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};  // [prec][out parity]
+    // grid-reduction scratch
+    wl::RedScratch red = {nullptr, nullptr, 0};
+    int red_slots = 0;
+    int red_gen = 0;  // bumped whenever the scratch moves (captured graphs hold its address)
+    // odd-parity temporaries for wilson_mult (eo = 1), per precision
+    void* tmp[3] = {nullptr, nullptr, nullptr};
+    size_t tmp_bytes[3] = {0, 0, 0};
+    wl::Timing timing;
+    wl::Workspace* ws = nullptr;  // solver workspace, owned (solver.cu)
+    std::map<std::string, wl::Tuned> tuned;
+};
+
+namespace wl {
+
+Geom make_geom(const int* dims);
+
+// Make sure the reduction scratch holds `slots` slots of `blocks` blocks.
+int ensure_red(wl_gauge g, int slots, long long blocks);
+// Make sure g->tmp[prec] holds at least `bytes`.
+int ensure_tmp(wl_gauge g, int prec, size_t bytes);
+
+// Hopping kernel launch description.  Fields are per output parity where an
+// array of two is given; strides are bytes between right-hand sides.
+struct HopLaunch {
+    int prec = WL_F32;
+    int dagger = 0;
+    int parity0 = 0;   // first output parity
+    int nparity = 1;   // 1 or 2 (both parities in one launch: the full D)
+    int nrhs = 1;
+    const void* in[2] = {nullptr, nullptr};
+    void* out[2] = {nullptr, nullptr};
+    const void* x1[2] = {nullptr, nullptr};  // out = x1 + b1 * x2 + a * H in
+    const void* x2[2] = {nullptr, nullptr};
+    const void* w[2] = {nullptr, nullptr};   // fused (w, out) and ||out||^2
+    long long rs_in = 0, rs_out = 0, rs_x1 = 0, rs_x2 = 0, rs_w = 0;
+    double a = 1.0, b1 = 0.0;
+    bool dot = false;
+    double* dot_out = nullptr;  // 3 doubles per rhs, stride dot_stride doubles
+    int dot_stride = 3;
+    const int* active = nullptr;  // skip right-hand sides whose flag is 0
+    int active_stride = 1;
+};
+
+int launch_hop(wl_gauge g, const HopLaunch& h, cudaStream_t s);
+
+// record-or-not helpers for per-launch timing
+void timing_begin(wl_gauge g, cudaStream_t s, double bytes, int prec, int* slot);
+void timing_end(wl_gauge g, cudaStream_t s, int slot);
+
+// BLAS-1 / reductions (blas.cu).  Vectors are `nhalf` half fields per rhs
+// back to back; rhs stride = nhalf * spinor_field_bytes(prec, Vh).
+// A stride argument of 0 selects the default (nhalf half fields per rhs).
+int launch_cdot(wl_gauge g, int prec, const void* a, const void* b, int nhalf, int nrhs,
+                double* out, int out_stride, const int* mask, cudaStream_t s, long long rs = 0);
+int launch_convert(wl_gauge g, int pdst, void* dst, int psrc, const void* src, int nhalf, int nrhs,
+                   const int* mask, cudaStream_t s, long long dst_rs = 0, long long src_rs = 0);
+int launch_zero(wl_gauge g, int prec, void* dst, int nhalf, int nrhs, const int* mask,
+                cudaStream_t s);
+// x_hi (F64) += x_lo (prec)
+int launch_accum_hi(wl_gauge g, double* xhi, int plo, const void* xlo, int nhalf, int nrhs,
+                    const int* mask, cudaStream_t s, long long hi_rs = 0);
+
+bool is_capturing(cudaStream_t s);
+
+}  // namespace wl

@@ -1,0 +1,47 @@
+"""bench.py's N>1 path on CPU: two gloo ranks; bytes add up over ranks and the
+step time is the slowest rank's (weak scaling, no data-path collective)."""
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import bench
+    r, w, _ = bench.dist_env()
+    bench.dist_init(w, "gloo")
+    total, ms = bench.aggregate(1e9 * (r + 1), 10.0 + 5 * r, w)
+    bench.barrier(w)
+    q.put((r, total, ms))
+    dist.destroy_process_group()
+
+
+def test_two_rank_aggregation():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r, total, ms in res:
+        assert total == pytest.approx(3e9)
+        assert ms == pytest.approx(15.0)
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.aggregate(5.0, 2.0, 1) == (5.0, 2.0)
