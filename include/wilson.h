@@ -130,6 +130,29 @@ int wilson_mult(wl_gauge g, void* out, const void* in, int eo, int dagger, wl_pr
 int wl_cdot(wl_gauge g, double* out, const void* a, const void* b, wl_prec prec, int nrhs,
             void* stream);
 
+/* Limits of wl_cdot_noalloc's built-in scratch. */
+#define WL_NOALLOC_MAX_RHS 64
+#define WL_NOALLOC_BLOCKS 512
+
+/* wl_cdot without any device allocation.  The paper has no counterpart: this
+ * is a library facility for callers that cannot allocate device memory --
+ * code running inside another framework's memory pool that must not call
+ * cudaMalloc behind it, latency-critical loops in which cudaMalloc/cudaFree
+ * would synchronise the device, and callers holding raw field pointers but no
+ * gauge object (wl_cdot keeps its scratch in the gauge object's workspace).
+ * Same results as wl_cdot (up to summation order) for nrhs half fields of Vh
+ * sites, stored back to back with stride wl_field_bytes(g, prec, 1); `out` is
+ * device memory for 3*nrhs doubles.  Scratch is one fixed __device__ array of
+ * WL_NOALLOC_MAX_RHS x WL_NOALLOC_BLOCKS x 3 doubles (768 KiB) that every GPU
+ * loading the library holds until the process exits; nrhs above
+ * WL_NOALLOC_MAX_RHS returns WL_ERR_ARG.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress), so make that first
+ * call before any stream capture.  All calls share the array and each call
+ * overwrites what the previous one left: calls that overlap on the GPU race.
+ * Never calls cudaMalloc, cudaFree or any allocating routine.  Asynchronous. */
+int wl_cdot_noalloc(double* out, const void* a, const void* b, long long Vh, wl_prec prec,
+                    int nrhs, void* stream);
+
 typedef struct {
     double tol;        /* stop when ||b - D x||_2 / ||b||_2 <= tol (full D, FP64), per RHS */
     int maxiter;       /* bound on inner iterations, per RHS */

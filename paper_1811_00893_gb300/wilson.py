@@ -84,6 +84,7 @@ def load() -> ctypes.CDLL:
             "wilson_dslash": (I, [P, P, P, I, I, I, I, P]),
             "wilson_mult": (I, [P, P, P, I, I, I, I, P]),
             "wl_cdot": (I, [P, P, P, P, I, I, P]),
+            "wl_cdot_noalloc": (I, [P, P, P, LL, I, I, P]),
             "wilson_solve": (I, [P, P, P, I, ctypes.POINTER(wl_solve_params),
                                  ctypes.POINTER(wl_solve_info), P]),
             "wilson_solve_batch": (I, [I, P, P, P, P, ctypes.POINTER(wl_solve_params),
@@ -106,7 +107,7 @@ def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["wl_gauge_create", "wl_gauge_destroy", "wl_half_volume", "wl_field_bytes",
             "wl_field_to_internal", "wl_field_to_canonical", "wilson_dslash", "wilson_mult",
-            "wl_cdot", "wilson_solve", "wilson_solve_batch", "wl_last_error",
+            "wl_cdot", "wl_cdot_noalloc", "wilson_solve", "wilson_solve_batch", "wl_last_error",
             "wl_launch_count", "wl_algorithmic_bytes", "wl_timing", "wl_timing_read"]
 
 
@@ -187,6 +188,13 @@ def wilson_mult(g, out, inp, eo: int, dagger: int, prec: int, nrhs: int, stream=
 
 def wl_cdot(g, out, a, b, prec: int, nrhs: int, stream=None) -> None:
     _check(load().wl_cdot(g, _ptr(out), _ptr(a), _ptr(b), int(prec), int(nrhs), _stream(stream)))
+
+
+def wl_cdot_noalloc(out, a, b, Vh: int, prec: int, nrhs: int, stream=None) -> None:
+    """wl_cdot for callers that cannot allocate device memory (fixed built-in
+    scratch, at most 64 right-hand sides, concurrent calls race)."""
+    _check(load().wl_cdot_noalloc(_ptr(out), _ptr(a), _ptr(b), int(Vh), int(prec), int(nrhs),
+                                  _stream(stream)))
 
 
 def solve_params(tol=1e-10, maxiter=20000, eo=True, inner=WL_F64, inner_tol=0.0, delta=0.0,
