@@ -51,6 +51,12 @@ _SIG = {
     "orc_true_residual": ("D", ["P", "P", "P", "P", "P", "D"]),
     "orc_solve": ("I", ["P", "P", "P", "P", "P", "D", "I", "D", "I", "P", "P"]),
     "orc_bicgstab_fixed": ("I", ["P", "P", "P", "P", "P", "D", "I", "I"]),
+    "orc_clover_true_residual": ("D", ["P", "P", "P", "P", "P", "P", "D"]),
+    "orc_clover_solve": ("I", ["P", "P", "P", "P", "P", "P", "D", "I", "D", "I", "P", "P"]),
+    "orc_clover_bicgstab_fixed": ("I", ["P", "P", "P", "P", "P", "P", "D", "I", "I"]),
+    "orc_clover_D_full": (None, ["P", "P", "P", "P", "P", "P", "D", "I"]),
+    "orc_clover_diag": (None, ["P", "P", "P", "P", "I", "I"]),
+    "orc_clover_Mee": (None, ["P", "P", "P", "P", "P", "P", "D"]),
 }
 _CT = {"P": ctypes.c_void_p, "I": ctypes.c_int, "D": ctypes.c_double, "L": ctypes.c_long}
 
@@ -249,4 +255,64 @@ def bicgstab_fixed(U, b_sys, dims, bc, kappa: float, eo: bool, niter: int):
     x = np.zeros_like(b)
     _load().orc_bicgstab_fixed(_p(U), _p(b), _p(x), _p(d), _p(bb), float(kappa),
                                int(bool(eo)), int(niter))
+    return x
+
+
+# ---------------------------------------------------------------------------
+# clover term (Eq. 2): F has shape (V, 2, 6, 6), block b acting on spins
+# {2b, 2b+1} x colour, row index local_spin*3 + colour
+# ---------------------------------------------------------------------------
+
+def clover_D_full(U, F, psi, dims, bc, kappa: float, dagger: bool = False) -> np.ndarray:
+    """D_clov psi = D_W psi + F psi (Eq. 2)."""
+    d, b, U, F, psi = _dims(dims), _bc(bc), _c(U), _c(F), _c(psi)
+    out = np.empty_like(psi)
+    _load().orc_clover_D_full(_p(U), _p(F), _p(psi), _p(out), _p(d), _p(b), float(kappa),
+                              -1 if dagger else 1)
+    return out
+
+
+def clover_diag(F, psi_half, dims, parity: int, inverse: bool = False) -> np.ndarray:
+    """(1 + F) psi or (1 + F)^{-1} psi on the sites of one parity."""
+    d, F, psi = _dims(dims), _c(F), _c(psi_half)
+    out = np.empty_like(psi)
+    _load().orc_clover_diag(_p(F), _p(psi), _p(out), _p(d), int(parity), int(bool(inverse)))
+    return out
+
+
+def clover_Mee(U, F, psi_e, dims, bc, kappa: float) -> np.ndarray:
+    """Schur complement A_ee - kappa^2 H_eo A_oo^{-1} H_oe with A = 1 + F."""
+    d, b, U, F, psi = _dims(dims), _bc(bc), _c(U), _c(F), _c(psi_e)
+    out = np.empty_like(psi)
+    _load().orc_clover_Mee(_p(U), _p(F), _p(psi), _p(out), _p(d), _p(b), float(kappa))
+    return out
+
+
+def clover_true_residual(U, F, b, x, dims, bc, kappa: float) -> float:
+    """||b - D_clov x||_2 / ||b||_2 on the full lattice."""
+    d, bb, U, F, b, x = _dims(dims), _bc(bc), _c(U), _c(F), _c(b), _c(x)
+    return float(_load().orc_clover_true_residual(_p(U), _p(F), _p(b), _p(x), _p(d), _p(bb),
+                                                  float(kappa)))
+
+
+def clover_solve(U, F, b, dims, bc, kappa: float, eo: bool = True, tol: float = 1e-10,
+                 maxiter: int = 10000, x0=None):
+    """Solve D_clov x = b by BiCGStab (full or even-odd Schur system)."""
+    d, bb, U, F, b = _dims(dims), _bc(bc), _c(U), _c(F), _c(b)
+    x = np.zeros_like(b) if x0 is None else _c(x0).copy()
+    info = np.zeros(4, np.int32)
+    res = np.zeros(1, np.float64)
+    rc = _load().orc_clover_solve(_p(U), _p(F), _p(b), _p(x), _p(d), _p(bb), float(kappa),
+                                  int(bool(eo)), float(tol), int(maxiter), _p(info), _p(res))
+    return x, {"status": int(rc), "iters": int(info[0]), "restarts": int(info[1]),
+               "bicgstab_status": int(info[2]), "passes": int(info[3]),
+               "true_resid": float(res[0])}
+
+
+def clover_bicgstab_fixed(U, F, b_sys, dims, bc, kappa: float, eo: bool, niter: int):
+    """Exactly ``niter`` BiCGStab iterations on D_clov or its Schur complement."""
+    d, bb, U, F, b = _dims(dims), _bc(bc), _c(U), _c(F), _c(b_sys)
+    x = np.zeros_like(b)
+    _load().orc_clover_bicgstab_fixed(_p(U), _p(F), _p(b), _p(x), _p(d), _p(bb), float(kappa),
+                                      int(bool(eo)), int(niter))
     return x

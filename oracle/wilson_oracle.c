@@ -363,14 +363,26 @@ typedef struct {
     const double* bc;
     double kappa;
     int eo; /* 0: full D, 1: M_ee */
+    const double* F; /* clover term of Eq. 2, or NULL for the Wilson matrix */
 } op_ctx;
+
+void orc_clover_D_full(const double* U, const double* F, const double* in, double* out,
+                       const int* L, const double* bc, double kappa, int d);
+void orc_clover_Mee(const double* U, const double* F, const double* in_e, double* out_e,
+                    const int* L, const double* bc, double kappa);
 
 static void apply_op(const op_ctx* c, const double* in, double* out)
 {
-    if (c->eo)
+    if (c->F) {
+        if (c->eo)
+            orc_clover_Mee(c->U, c->F, in, out, c->L, c->bc, c->kappa);
+        else
+            orc_clover_D_full(c->U, c->F, in, out, c->L, c->bc, c->kappa, +1);
+    } else if (c->eo) {
         orc_Mee(c->U, in, out, c->L, c->bc, c->kappa, +1);
-    else
+    } else {
         orc_D_full(c->U, in, out, c->L, c->bc, c->kappa, +1);
+    }
 }
 
 /* Solve A x = b until ||b - A x||_2 <= tol_abs (the recursively updated
@@ -553,6 +565,240 @@ int orc_bicgstab_fixed(const double* U, const double* b_sys, double* x_sys, cons
 {
     long n = (eo ? volume(L) / 2 : volume(L)) * NS * NC;
     op_ctx c = {U, L, bc, kappa, eo};
+    int iters = 0, restarts = 0;
+    return bicgstab(&c, n, b_sys, x_sys, 0.0, niter, &iters, &restarts);
+}
+
+/* ------------------------------------------------------------------ */
+/* clover term (Eq. 2)                                                 */
+/* ------------------------------------------------------------------ */
+
+/* Eq. 2, Sec. 2 "Clover Fermion Matrix": D_clov(x,y) = D_W(x,y) + F(x) delta_xy
+ * with F(x) a 12x12 Hermitian matrix that, in a suitable basis, is block
+ * diagonal with two 6x6 Hermitian blocks.  In the chiral basis used here the
+ * blocks act on spins {0,1} and {2,3}: F[s][b][i][j] (complex) with
+ * i, j = local_spin*3 + colour.  F is an input field, like U (the paper
+ * ignores its construction).  The oracle expands it to a full 12x12 matrix
+ * and multiplies it literally. */
+#define CLOVER_REALS (2 * 2 * 6 * 6) /* two 6x6 complex blocks per site */
+
+static void clover_matrix(const double* Fs, double M[12][12][2])
+{
+    for (int i = 0; i < 12; ++i)
+        for (int j = 0; j < 12; ++j) M[i][j][0] = M[i][j][1] = 0.0;
+    for (int b = 0; b < 2; ++b)
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                M[6 * b + i][6 * b + j][0] = Fs[2 * ((b * 6 + i) * 6 + j)];
+                M[6 * b + i][6 * b + j][1] = Fs[2 * ((b * 6 + i) * 6 + j) + 1];
+            }
+}
+
+/* out_site += M v (12x12 complex times a 12-component site vector) */
+static void add_matvec12(double M[12][12][2], const double* v, double* out_site)
+{
+    for (int i = 0; i < 12; ++i) {
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < 12; ++j) {
+            re += M[i][j][0] * v[2 * j] - M[i][j][1] * v[2 * j + 1];
+            im += M[i][j][0] * v[2 * j + 1] + M[i][j][1] * v[2 * j];
+        }
+        out_site[2 * i] += re;
+        out_site[2 * i + 1] += im;
+    }
+}
+
+/* out = D_clov in = D_W in + F in (Eq. 2 with D_W of Eq. 1).  F is
+ * Hermitian, so the adjoint operator (d = -1) adds the same F. */
+void orc_clover_D_full(const double* U, const double* F, const double* in, double* out,
+                       const int* L, const double* bc, double kappa, int d)
+{
+    long V = volume(L);
+    orc_D_full(U, in, out, L, bc, kappa, d);
+#pragma omp parallel for schedule(static)
+    for (long s = 0; s < V; ++s) {
+        double M[12][12][2];
+        clover_matrix(F + s * CLOVER_REALS, M);
+        add_matvec12(M, in + s * SITE_REALS, out + s * SITE_REALS);
+    }
+}
+
+/* Solve the 12x12 complex system A y = v by Gaussian elimination with
+ * partial pivoting (A = 1 + F(x) at one site). */
+static void solve12(double A_in[12][12][2], const double* v, double* y)
+{
+    double A[12][13][2];
+    for (int i = 0; i < 12; ++i) {
+        for (int j = 0; j < 12; ++j) {
+            A[i][j][0] = A_in[i][j][0];
+            A[i][j][1] = A_in[i][j][1];
+        }
+        A[i][12][0] = v[2 * i];
+        A[i][12][1] = v[2 * i + 1];
+    }
+    for (int c = 0; c < 12; ++c) {
+        int piv = c;
+        double best = A[c][c][0] * A[c][c][0] + A[c][c][1] * A[c][c][1];
+        for (int r = c + 1; r < 12; ++r) {
+            double m = A[r][c][0] * A[r][c][0] + A[r][c][1] * A[r][c][1];
+            if (m > best) { best = m; piv = r; }
+        }
+        if (piv != c)
+            for (int j = 0; j < 13; ++j) {
+                double t0 = A[c][j][0], t1 = A[c][j][1];
+                A[c][j][0] = A[piv][j][0];
+                A[c][j][1] = A[piv][j][1];
+                A[piv][j][0] = t0;
+                A[piv][j][1] = t1;
+            }
+        for (int r = c + 1; r < 12; ++r) {
+            /* f = A[r][c] / A[c][c] */
+            double den = A[c][c][0] * A[c][c][0] + A[c][c][1] * A[c][c][1];
+            double fr = (A[r][c][0] * A[c][c][0] + A[r][c][1] * A[c][c][1]) / den;
+            double fi = (A[r][c][1] * A[c][c][0] - A[r][c][0] * A[c][c][1]) / den;
+            for (int j = c; j < 13; ++j) {
+                A[r][j][0] -= fr * A[c][j][0] - fi * A[c][j][1];
+                A[r][j][1] -= fr * A[c][j][1] + fi * A[c][j][0];
+            }
+        }
+    }
+    for (int i = 11; i >= 0; --i) {
+        double re = A[i][12][0], im = A[i][12][1];
+        for (int j = i + 1; j < 12; ++j) {
+            re -= A[i][j][0] * y[2 * j] - A[i][j][1] * y[2 * j + 1];
+            im -= A[i][j][0] * y[2 * j + 1] + A[i][j][1] * y[2 * j];
+        }
+        double den = A[i][i][0] * A[i][i][0] + A[i][i][1] * A[i][i][1];
+        y[2 * i] = (re * A[i][i][0] + im * A[i][i][1]) / den;
+        y[2 * i + 1] = (im * A[i][i][0] - re * A[i][i][1]) / den;
+    }
+}
+
+/* The site-diagonal part of D_clov on one parity: out = (1 + F) in
+ * (inverse = 0) or out = (1 + F)^{-1} in (inverse = 1), half fields. */
+void orc_clover_diag(const double* F, const double* in_half, double* out_half, const int* L,
+                     int parity, int inverse)
+{
+    long Vh = volume(L) / 2;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < Vh; ++i) {
+        long s = site_of_half(L, i, parity);
+        double M[12][12][2];
+        clover_matrix(F + s * CLOVER_REALS, M);
+        for (int k = 0; k < 12; ++k) M[k][k][0] += 1.0;
+        double* o = out_half + i * SITE_REALS;
+        if (inverse) {
+            solve12(M, in_half + i * SITE_REALS, o);
+        } else {
+            for (int k = 0; k < SITE_REALS; ++k) o[k] = 0.0;
+            add_matvec12(M, in_half + i * SITE_REALS, o);
+        }
+    }
+}
+
+/* Schur complement of D_clov on the even sites:
+ *   M_ee = A_ee - kappa^2 H_eo A_oo^{-1} H_oe,   A = 1 + F. */
+void orc_clover_Mee(const double* U, const double* F, const double* in_e, double* out_e,
+                    const int* L, const double* bc, double kappa)
+{
+    long Vh = volume(L) / 2;
+    size_t hb = sizeof(double) * Vh * SITE_REALS;
+    double* t1 = (double*)malloc(hb);
+    double* t2 = (double*)malloc(hb);
+    orc_hop_eo(U, in_e, t1, L, bc, 1, +1);   /* t1 = H_oe in       */
+    orc_clover_diag(F, t1, t2, L, 1, 1);     /* t2 = A_oo^-1 t1    */
+    orc_hop_eo(U, t2, t1, L, bc, 0, +1);     /* t1 = H_eo t2       */
+    orc_clover_diag(F, in_e, out_e, L, 0, 0); /* out = A_ee in     */
+    for (long k = 0; k < Vh * SITE_REALS; ++k) out_e[k] -= kappa * kappa * t1[k];
+    free(t1);
+    free(t2);
+}
+
+/* ------------------------------------------------------------------ */
+/* clover solve (Eq. 2 inside the BiCGStab of Sec. 2)                  */
+/* ------------------------------------------------------------------ */
+
+/* ||b - D_clov x||_2 / ||b||_2 on the full lattice. */
+double orc_clover_true_residual(const double* U, const double* F, const double* b,
+                                const double* x, const int* L, const double* bc, double kappa)
+{
+    long V = volume(L);
+    double* r = (double*)malloc(sizeof(double) * V * SITE_REALS);
+    orc_clover_D_full(U, F, x, r, L, bc, kappa, +1);
+    for (long k = 0; k < V * SITE_REALS; ++k) r[k] = b[k] - r[k];
+    double rr = norm2(V * NS * NC, r), bb = norm2(V * NS * NC, b);
+    free(r);
+    return sqrt(rr / bb);
+}
+
+/* Solve D_clov x = b to a true relative residual <= tol.  With A = 1 + F:
+ *   eo = 0: BiCGStab on D_clov itself;
+ *   eo = 1: write D_clov in even/odd blocks [[A_ee, -k H_eo], [-k H_oe, A_oo]];
+ *           eliminating x_o = A_oo^-1 (b_o + k H_oe x_e) leaves
+ *           (A_ee - k^2 H_eo A_oo^-1 H_oe) x_e = b_e + k H_eo A_oo^-1 b_o.
+ * Same conventions for x, info and true_resid as orc_solve. */
+int orc_clover_solve(const double* U, const double* F, const double* b, double* x, const int* L,
+                     const double* bc, double kappa, int eo, double tol, int maxiter, int* info,
+                     double* true_resid)
+{
+    long V = volume(L), Vh = V / 2;
+    op_ctx c = {U, L, bc, kappa, eo, F};
+    int iters = 0, restarts = 0, status = 1, passes = 0;
+    double bnorm = sqrt(norm2(V * NS * NC, b));
+    double target = tol * bnorm;
+    double res = 1.0;
+    if (bnorm == 0.0) {
+        memset(x, 0, sizeof(double) * V * SITE_REALS);
+        info[0] = info[1] = info[2] = info[3] = 0;
+        *true_resid = 0.0;
+        return 0;
+    }
+    if (!eo) {
+        for (passes = 0; passes < 4; ++passes) {
+            status = bicgstab(&c, V * NS * NC, b, x, target, maxiter - iters, &iters, &restarts);
+            res = orc_clover_true_residual(U, F, b, x, L, bc, kappa);
+            if (res <= tol || status != 0) break;
+            target *= 0.1;
+        }
+    } else {
+        size_t hb = sizeof(double) * Vh * SITE_REALS;
+        double* be = (double*)malloc(hb);
+        double* bo = (double*)malloc(hb);
+        double* xe = (double*)malloc(hb);
+        double* xo = (double*)malloc(hb);
+        double* t1 = (double*)malloc(hb);
+        double* t2 = (double*)malloc(hb);
+        orc_split(L, b, be, bo);
+        orc_split(L, x, xe, xo);
+        orc_clover_diag(F, bo, t1, L, 1, 1);  /* t1 = A_oo^-1 b_o       */
+        orc_hop_eo(U, t1, t2, L, bc, 0, +1);  /* t2 = H_eo A_oo^-1 b_o  */
+        for (long k = 0; k < Vh * SITE_REALS; ++k) be[k] += kappa * t2[k];
+        for (passes = 0; passes < 4; ++passes) {
+            status = bicgstab(&c, Vh * NS * NC, be, xe, target, maxiter - iters, &iters, &restarts);
+            orc_hop_eo(U, xe, t1, L, bc, 1, +1); /* t1 = H_oe x_e */
+            for (long k = 0; k < Vh * SITE_REALS; ++k) t1[k] = bo[k] + kappa * t1[k];
+            orc_clover_diag(F, t1, xo, L, 1, 1); /* x_o = A_oo^-1 (b_o + k H_oe x_e) */
+            orc_join(L, xe, xo, x);
+            res = orc_clover_true_residual(U, F, b, x, L, bc, kappa);
+            if (res <= tol || status != 0) break;
+            target *= 0.1;
+        }
+        free(be); free(bo); free(xe); free(xo); free(t1); free(t2);
+    }
+    info[0] = iters;
+    info[1] = restarts;
+    info[2] = status;
+    info[3] = passes + 1;
+    *true_resid = res;
+    return (res <= tol) ? 0 : (status ? status : 3);
+}
+
+/* orc_bicgstab_fixed for D_clov (eo = 0) or its Schur complement (eo = 1). */
+int orc_clover_bicgstab_fixed(const double* U, const double* F, const double* b_sys, double* x_sys,
+                              const int* L, const double* bc, double kappa, int eo, int niter)
+{
+    long n = (eo ? volume(L) / 2 : volume(L)) * NS * NC;
+    op_ctx c = {U, L, bc, kappa, eo, F};
     int iters = 0, restarts = 0;
     return bicgstab(&c, n, b_sys, x_sys, 0.0, niter, &iters, &restarts);
 }

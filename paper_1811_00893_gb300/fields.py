@@ -61,12 +61,19 @@ def _gram_schmidt(Z: torch.Tensor) -> torch.Tensor:
     return torch.stack([q0, q1, q2], dim=-1)
 
 
+def det3(M: torch.Tensor) -> torch.Tensor:
+    """Determinant of each 3x3 matrix by cofactor expansion along the first row."""
+    return (M[..., 0, 0] * (M[..., 1, 1] * M[..., 2, 2] - M[..., 1, 2] * M[..., 2, 1])
+            - M[..., 0, 1] * (M[..., 1, 0] * M[..., 2, 2] - M[..., 1, 2] * M[..., 2, 0])
+            + M[..., 0, 2] * (M[..., 1, 0] * M[..., 2, 1] - M[..., 1, 1] * M[..., 2, 0]))
+
+
 def unitarise(Z: torch.Tensor) -> torch.Tensor:
     """Q factor of Z = QR with R's diagonal real positive (Gram-Schmidt on the
     columns, repeated once to restore orthogonality lost to rounding), then
     divided by the principal cube root of its determinant."""
     Q = _gram_schmidt(_gram_schmidt(Z))
-    theta = torch.angle(torch.linalg.det(Q))
+    theta = torch.angle(det3(Q))
     return Q * torch.polar(torch.ones_like(theta), -theta / 3.0)[..., None, None]
 
 
@@ -95,6 +102,23 @@ def gell_mann(device="cpu") -> torch.Tensor:
     return torch.from_numpy(l).to(device)
 
 
+def expm(X: torch.Tensor, order: int = 16) -> torch.Tensor:
+    """exp of each 3x3 matrix: scale by 2^-k so that ||X||_F <= 1/2, Taylor
+    series to `order` (truncation < 0.5^17/17! ~ 2e-20), square k times."""
+    nrm = torch.linalg.vector_norm(X.reshape(X.shape[0], -1), dim=-1).max().item()
+    k = max(0, int(math.ceil(math.log2(nrm / 0.5)))) if nrm > 0.5 else 0
+    Y = X / (2.0 ** k)
+    I = torch.eye(3, dtype=X.dtype, device=X.device).expand_as(X)
+    term = I.clone()
+    E = I.clone()
+    for n in range(1, order + 1):
+        term = torch.bmm(term, Y) / n
+        E = E + term
+    for _ in range(k):
+        E = torch.bmm(E, E)
+    return E
+
+
 def smooth_su3(n: int, gen: torch.Generator, device="cpu", eps: float = 0.3) -> torch.Tensor:
     """n matrices exp(i eps A), A = sum_a omega_a lambda_a/2, shape (n, 3, 3)."""
     lam = gell_mann(device) / 2.0
@@ -103,7 +127,7 @@ def smooth_su3(n: int, gen: torch.Generator, device="cpu", eps: float = 0.3) -> 
         b = min(n, a + CHUNK)
         w = torch.randn((b - a, 8), generator=gen, dtype=torch.float64, device=device)
         A = torch.einsum("na,aij->nij", w.to(torch.complex128), lam)
-        out[a:b] = unitarise(torch.linalg.matrix_exp(1j * eps * A))
+        out[a:b] = unitarise(expm(1j * eps * A))
     return out
 
 
@@ -133,6 +157,16 @@ def gaussian_fermion(dims, nrhs: int, seed: int, device="cpu") -> torch.Tensor:
     for j in range(nrhs):
         out[j] = _cgauss((V, 4, 3), generator(seed + j, device), device)
     return out
+
+
+def clover_field(dims, seed: int, device="cpu", scale: float = 0.1) -> torch.Tensor:
+    """Synthetic clover term F(x) of Eq. 2: two Hermitian 6x6 blocks per site,
+    shape (V, 2, 6, 6), each scale * (Z + Z^dag)/2 with Z complex Gaussian of
+    unit-variance entries / sqrt(6).  (The paper takes F as a precomputed
+    input and ignores how it is built.)"""
+    V = volume(dims)
+    Z = _cgauss((V, 2, 6, 6), generator(seed, device), device) / math.sqrt(12.0)
+    return scale * 0.5 * (Z + Z.conj().transpose(-1, -2))
 
 
 def gauge_transform(dims, seed: int, device="cpu") -> torch.Tensor:

@@ -44,6 +44,19 @@ def test_smooth_links():
     assert torch.allclose(tr, 2 * torch.eye(8, dtype=tr.dtype), atol=1e-14)
 
 
+def test_expm_matches_library_exponential():
+    w = torch.randn((2000, 8), generator=fields.generator(7), dtype=torch.float64)
+    A = torch.einsum("na,aij->nij", w.to(torch.complex128), fields.gell_mann() / 2)
+    for eps in (0.3, 3.0):
+        X = 1j * eps * A
+        assert torch.allclose(fields.expm(X), torch.linalg.matrix_exp(X), rtol=0, atol=1e-13)
+
+
+def test_det3_matches_library_determinant():
+    Z = fields._cgauss((1000, 3, 3), fields.generator(6), "cpu")
+    assert torch.allclose(fields.det3(Z), torch.linalg.det(Z), rtol=1e-12, atol=1e-12)
+
+
 def test_seeded_reproducible():
     a = fields.gauge_field((4, 2, 2, 2), "haar", 9)
     b = fields.gauge_field((4, 2, 2, 2), "haar", 9)

@@ -12,6 +12,7 @@ import tempfile
 import pytest
 
 import oracle
+import oracle_clover_pins as C
 import oracle_pins as P
 
 MUTANTS = {
@@ -44,6 +45,21 @@ MUTANTS = {
                                    "si += a[2 * i] * b[2 * i + 1] + a[2 * i + 1] * b[2 * i];"),
     "half index parity": ("return parity_of(L, s) == p ? s : s + 1;",
                           "return parity_of(L, s) != p ? s : s + 1;"),
+    "clover block transposed": ("M[6 * b + i][6 * b + j][1] = Fs[2 * ((b * 6 + i) * 6 + j) + 1];",
+                                "M[6 * b + i][6 * b + j][1] = Fs[2 * ((b * 6 + j) * 6 + i) + 1];"),
+    "clover block on the wrong spins": ("M[6 * b + i][6 * b + j][0] = Fs[2 * ((b * 6 + i) * 6 + j)];",
+                                        "M[6 * (1 - b) + i][6 * (1 - b) + j][0] = Fs[2 * ((b * 6 + i) * 6 + j)];"),
+    "clover product conjugated": ("im += M[i][j][0] * v[2 * j + 1] + M[i][j][1] * v[2 * j];",
+                                  "im += M[i][j][0] * v[2 * j + 1] - M[i][j][1] * v[2 * j];"),
+    "clover Schur without inverse": ("orc_clover_diag(F, t1, t2, L, 1, 1);",
+                                     "orc_clover_diag(F, t1, t2, L, 1, 0);"),
+    "clover even-odd source without inverse": ("orc_clover_diag(F, bo, t1, L, 1, 1);",
+                                               "orc_clover_diag(F, bo, t1, L, 1, 0);"),
+    "clover reconstruction without inverse": ("orc_clover_diag(F, t1, xo, L, 1, 1);",
+                                              "orc_clover_diag(F, t1, xo, L, 1, 0);"),
+    "clover solve on the Wilson matrix": ("    if (c->F) {", "    if (0) {"),
+    "clover back substitution sign": ("re -= A[i][j][0] * y[2 * j] - A[i][j][1] * y[2 * j + 1];",
+                                      "re += A[i][j][0] * y[2 * j] - A[i][j][1] * y[2 * j + 1];"),
 }
 
 
@@ -63,9 +79,9 @@ def test_planted_mistake_is_caught(name, source):
             f.write(source.replace(old, new))
         lib = oracle.compile_source(src, os.path.join(d, "libmutant.so"))
         with oracle.use_library(lib):
-            failed = P.failing_checks()
+            failed = P.failing_checks(P.ALL_CHECKS + C.CLOVER_CHECKS)
     assert failed, f"no pin notices the planted mistake {name!r}"
 
 
 def test_unmutated_source_passes_all_checks():
-    assert P.failing_checks() == []
+    assert P.failing_checks(P.ALL_CHECKS + C.CLOVER_CHECKS) == []
