@@ -43,7 +43,8 @@ UNIT = "GB/s"
 FALLBACK_HBM_GBS = 6800.0
 WORKLOAD_INDEX = 1  # 32^3x64 even-odd, FP32 inner, FP64 defect correction
 PROFILE = os.path.join(ROOT, "profiles", "hop_f32_32x32x32x64.md")
-KERNEL_SOURCES = ["paper_1811_00893_gb300/csrc/dslash.cu", "paper_1811_00893_gb300/csrc/common.cuh"]
+KERNEL_SOURCES = ["paper_1811_00893_gb300/csrc/dslash.cu", "paper_1811_00893_gb300/csrc/hop.cuh",
+                  "paper_1811_00893_gb300/csrc/common.cuh", "paper_1811_00893_gb300/csrc/df64.cuh"]
 
 
 def parse_args(argv=None):
@@ -56,6 +57,10 @@ def parse_args(argv=None):
                     help="skip the oracle sample (for quick runs)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target duration of the oracle sample")
+    ap.add_argument("--workload", type=int, default=WORKLOAD_INDEX,
+                    help="workload index (workloads.WORKLOADS); the default is the headline one")
+    ap.add_argument("--dims", type=str, default=None,
+                    help="override the lattice extents, e.g. 24,24,24,48 (smaller profiling runs)")
     return ap.parse_args(argv)
 
 
@@ -218,14 +223,26 @@ def make_inputs(wl, rank: int, device: str):
     return U, b
 
 
+SCHEMES = {  # workload scheme -> (inner precision name, solve parameters)
+    "fp64": ("f64", dict(eo=False, inner=0)),
+    "fp32-defect-correction": ("f32", dict(eo=True, inner=1)),
+    "fp16-reliable": ("f16", dict(eo=True, inner=2, delta=0.003)),
+    "fp32-multirhs": ("f32", dict(eo=True, inner=1, graph_iters=8)),
+}
+
+
 def config_of(wl):
-    return {"workload": f"{'x'.join(map(str, wl.dims))} Wilson even-odd, kappa={wl.kappa}, "
-                        f"{wl.links} links (eps=0.3), {wl.nrhs} Gaussian RHS; FP32 BiCGStab "
-                        f"+ FP64 defect correction to 1e-10 true residual",
+    from paper_1811_00893_gb300 import costs
+    prec, kw = SCHEMES[wl.scheme]
+    links = costs.link_bytes(prec) * 8 * wl.volume  # both parities
+    return {"workload": wl.name + f", kappa={wl.kappa}, {wl.links} links, {wl.nrhs} Gaussian "
+                                  f"RHS, to 1e-10 true residual",
             "dims": list(wl.dims), "kappa": wl.kappa, "bc": "periodic xyz, antiperiodic t",
-            "nrhs": wl.nrhs, "tol": 1e-10, "inner": "f32", "outer": "f64",
+            "nrhs": wl.nrhs, "tol": 1e-10, "inner": prec, "outer": "f64", "scheme": wl.scheme,
             "seeds": {"gauge": wl.gauge_seed, "source": wl.source_seed},
-            "l2": "inputs larger than L2 (FP32 links 604 MB, FP64 links 1208 MB per lattice)"}
+            "l2": (f"inputs larger than L2 ({prec.upper()} links {links / 1e6:.0f} MB)"
+                   if links > 129e6 else
+                   f"inputs smaller than L2 ({links / 1e6:.1f} MB of links): cache-resident")}
 
 
 def oracle_sample(wl, U_host, b_host, seconds: float):
@@ -234,20 +251,24 @@ def oracle_sample(wl, U_host, b_host, seconds: float):
     import oracle
     from paper_1811_00893_gb300 import costs
     oracle.build()
-    be, bo = oracle.split(b_host, wl.dims)
-    bsys = be + wl.kappa * oracle.hop_eo(U_host, bo, wl.dims, wl.bc, 0)
+    if wl.eo:
+        be, bo = oracle.split(b_host, wl.dims)
+        bsys = be + wl.kappa * oracle.hop_eo(U_host, bo, wl.dims, wl.bc, 0)
+    else:
+        bsys = b_host
     t0 = time.perf_counter()
-    oracle.bicgstab_fixed(U_host, bsys, wl.dims, wl.bc, wl.kappa, True, 1)
+    oracle.bicgstab_fixed(U_host, bsys, wl.dims, wl.bc, wl.kappa, wl.eo, 1)
     t1 = time.perf_counter() - t0
     n = int(max(1, min(60, seconds / max(t1, 1e-3))))
     t0 = time.perf_counter()
-    oracle.bicgstab_fixed(U_host, bsys, wl.dims, wl.bc, wl.kappa, True, n)
+    oracle.bicgstab_fixed(U_host, bsys, wl.dims, wl.bc, wl.kappa, wl.eo, n)
     dt = time.perf_counter() - t0
-    Vh = wl.volume // 2
-    per_iter = costs.bicgstab_iteration_bytes("f64", "f64") * Vh
+    sites = wl.volume // 2 if wl.eo else wl.volume
+    per_iter = costs.bicgstab_iteration_bytes("f64", "f64", eo=wl.eo) * sites
+    kind = "even-odd" if wl.eo else "full-D"
     return (n * per_iter / dt / 1e9, oracle.get_threads(),
-            f"{n} FP64 even-odd BiCGStab iterations of the oracle on the full "
-            f"{'x'.join(map(str, wl.dims))} lattice ({dt:.1f} s), bytes counted with the "
+            f"{n} FP64 {kind} BiCGStab iterations of the oracle (one right-hand side) on the "
+            f"full {'x'.join(map(str, wl.dims))} lattice ({dt:.1f} s), bytes counted with the "
             f"library's per-iteration model", dt / n)
 
 
@@ -263,17 +284,22 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     dist_init(world, "nccl")
     dev = f"cuda:{local}"
-    wl = WORKLOADS[WORKLOAD_INDEX]
+    wl = WORKLOADS[args.workload]
+    if args.dims:
+        import dataclasses
+        wl = dataclasses.replace(wl, dims=tuple(int(v) for v in args.dims.split(",")))
+    pname, pkw = SCHEMES[wl.scheme]
+    P = wilson.PREC[pname]
     U, b = make_inputs(wl, rank, dev)
     want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
     U_host = U.cpu().numpy() if want_cpu else None
     b_host = b[0].cpu().numpy() if want_cpu else None
-    g = wilson.Gauge(wl.dims, wl.kappa, U, precs=("f64", "f32"), bc=wl.bc)
+    g = wilson.Gauge(wl.dims, wl.kappa, U, precs=("f64", pname), bc=wl.bc)
     del U
     torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
     x = torch.zeros_like(b)
-    mixed = wilson.solve_params(tol=1e-10, eo=True, inner=wilson.WL_F32, graph_iters=0)
+    mixed = wilson.solve_params(tol=1e-10, **pkw)
 
     def solve(xx, bb, p=mixed):
         return wilson.wilson_solve(g.handle, xx, bb, wl.nrhs, p)
@@ -291,7 +317,7 @@ def run_ours(args, rank, world, local):
     infos = []
     for _ in range(args.steps):
         rc, info = solve(x, b)
-        infos.append(info[0])
+        infos.extend(info)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -300,8 +326,10 @@ def run_ours(args, rank, world, local):
     launches = wilson.wl_launch_count() - l0
     bytes_local = wilson.wl_algorithmic_bytes() - b0
     wilson.wl_timing(g.handle, False)
-    hop_ms, hop_n, hop_bytes = wilson.wl_timing_read(g.handle, wilson.WL_F32)
+    hop_ms, hop_n, hop_bytes = wilson.wl_timing_read(g.handle, P)
     h64_ms, h64_n, h64_bytes = wilson.wl_timing_read(g.handle, wilson.WL_F64)
+    if P == wilson.WL_F64:
+        h64_ms = 0.0
     total_bytes, ms = aggregate(bytes_local, ms_local, world, device=dev)
     ms_per_step = ms / args.steps
     value = total_bytes / (ms / 1e3) / 1e9
@@ -322,29 +350,32 @@ def run_ours(args, rank, world, local):
     nbytes_io = b.numel() * b.element_size()
 
     # ---------------- the paper's mult protocol: 1000 back-to-back hops
-    fin = g.field("f32")
-    fout = g.field("f32")
-    wilson.wl_field_to_internal(g.handle, fin, b, 1, wilson.WL_F32, 1)
+    nr = wl.nrhs
+    fin = g.field(pname, nr)
+    fout = g.field(pname, nr)
+    wilson.wl_field_to_internal(g.handle, fin, b, 1, P, nr)
     for _ in range(10):
-        wilson.wilson_dslash(g.handle, fout, fin, 0, 0, wilson.WL_F32, 1)
+        wilson.wilson_dslash(g.handle, fout, fin, 0, 0, P, nr)
     torch.cuda.synchronize()
     d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     d0.record(stream)
     for _ in range(1000):
-        wilson.wilson_dslash(g.handle, fout, fin, 0, 0, wilson.WL_F32, 1)
+        wilson.wilson_dslash(g.handle, fout, fin, 0, 0, P, nr)
     d1.record(stream)
     torch.cuda.synchronize()
     dslash_s = d0.elapsed_time(d1) / 1e3 / 1000
     Vh = wl.volume // 2
     peak, peak_kind = hbm_peak()
-    dslash_gbs = costs.hop_bytes_per_site("f32") * Vh / dslash_s / 1e9
-    dslash = {"gbs": dslash_gbs, "gflops": costs.FLOPS_HOP_SITE * Vh / dslash_s / 1e9,
+    bps = costs.hop_bytes_per_site(pname, nrhs=nr)
+    dslash_gbs = bps * Vh / dslash_s / 1e9
+    dslash = {"precision": pname, "nrhs": nr, "gbs": dslash_gbs,
+              "gflops": costs.FLOPS_HOP_SITE * Vh * nr / dslash_s / 1e9,
               "us_per_launch": dslash_s * 1e6, "frac_hbm": dslash_gbs / peak,
-              "bytes_per_site": costs.hop_bytes_per_site("f32"), "launches": 1000}
+              "bytes_per_site": bps, "launches": 1000}
 
     # ---------------- plain FP64 GPU solve for the time-to-solution comparison
     x64 = torch.zeros_like(b)
-    p64 = wilson.solve_params(tol=1e-10, eo=True, inner=wilson.WL_F64, graph_iters=0)
+    p64 = wilson.solve_params(tol=1e-10, eo=wl.eo, inner=wilson.WL_F64, graph_iters=0)
     solve(x64, b, p64)
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -362,18 +393,22 @@ def run_ours(args, rank, world, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "dtype_outer": "f64", "data": "synthetic",
+            "dtype": pname, "dtype_outer": "f64", "data": "synthetic",
             "config": config_of(wl),
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes_io,
                     "d2h_bytes_per_step": nbytes_io, "ms_per_step": e2e_ms,
                     "timer": "wall clock around wilson_solve with pinned host b and x"},
             "gpu_launches": launches,
-            "roofline": {"kernel": "hop_kernel<f32> (all hopping launches of the inner solve)",
-                         "bound": "hbm", "achieved": achieved, "peak": peak,
+            "roofline": {"kernel": (f"hop_kernel<{pname}>" if nr == 1 else
+                                    f"hop_mrhs_kernel<{pname}>") +
+                                   " (all hopping launches of the inner solve)",
+                         "bound": "alu" if P == wilson.WL_F64 else "hbm", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,
-                         "traffic": traffic, "launches": hop_n,
+                         "traffic": traffic if (P == wilson.WL_F32 and nr == 1
+                                                and wl.dims == (32, 32, 32, 64)) else None,
+                         "launches": hop_n,
                          "algorithmic_bytes_per_launch": hop_bytes / max(hop_n, 1),
                          "avg_us": hop_ms * 1e3 / max(hop_n, 1),
                          "share_of_step": hop_ms / ms_local if ms_local else None,
@@ -381,9 +416,11 @@ def run_ours(args, rank, world, local):
             "dslash": dslash,
             "solve": {"mixed_ms": ms_per_step, "fp64_ms": fp64_ms,
                       "speedup_vs_fp64": fp64_ms / ms_per_step,
-                      "mixed_iters": infos[-1]["iters"], "mixed_outer": infos[-1]["outer"],
+                      "mixed_iters": max(i["iters"] for i in infos[-nr:]),
+                      "mixed_outer": max(i["outer"] for i in infos[-nr:]),
                       "mixed_true_resid": max(i["true_resid"] for i in infos),
-                      "fp64_iters": info64[0]["iters"], "fp64_true_resid": info64[0]["true_resid"]},
+                      "fp64_iters": max(i["iters"] for i in info64),
+                      "fp64_true_resid": max(i["true_resid"] for i in info64)},
         }
         if want_cpu:
             gbs, cores, sample, s_per_iter = oracle_sample(wl, U_host, b_host, args.cpu_seconds)
@@ -392,6 +429,94 @@ def run_ours(args, rank, world, local):
         else:
             out["cpu_baseline"] = None
     g.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# the uneven multi-lattice batch
+# ---------------------------------------------------------------------------
+
+BATCH_INDEX = 4
+
+
+def run_batch(args, rank, world, local):
+    import torch
+    from paper_1811_00893_gb300 import fields, wilson, workloads
+
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = f"cuda:{local}"
+    spec = workloads.uneven_batch()
+    gs, bs, xs = [], [], []
+    for m in spec:
+        U = fields.gauge_field(m.dims, "haar", m.gauge_seed, device=dev)
+        gs.append(wilson.Gauge(m.dims, m.kappa, U, precs=("f64", "f32"), bc=workloads.BC_PPPA))
+        bs.append(fields.gaussian_fermion(m.dims, m.nrhs, m.source_seed + 100 * rank, device=dev))
+        xs.append(torch.zeros_like(bs[-1]))
+    hs = [g.handle for g in gs]
+    nr = [m.nrhs for m in spec]
+    p = wilson.solve_params(tol=1e-10, eo=True, inner=wilson.WL_F32, graph_iters=8)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        wilson.wilson_solve_batch(hs, xs, bs, nr, p)
+    clk = ClockSampler(gpu_index_for(local)).start()
+    l0, b0 = wilson.wl_launch_count(), wilson.wl_algorithmic_bytes()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        rc, infos = wilson.wilson_solve_batch(hs, xs, bs, nr, p)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    ms_local = e0.elapsed_time(e1)
+    launches = wilson.wl_launch_count() - l0
+    total_bytes, ms = aggregate(wilson.wl_algorithmic_bytes() - b0, ms_local, world, device=dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3
+
+    def per_lattice(inner, graph):
+        q = wilson.solve_params(tol=1e-10, eo=True, inner=inner, graph_iters=graph)
+        for g, x, b, n in zip(gs, xs, bs, nr):
+            wilson.wilson_solve(g.handle, x, b, n, q)
+
+    seq_mixed_ms = timed(lambda: per_lattice(wilson.WL_F32, 8))
+    seq_fp64_ms = timed(lambda: per_lattice(wilson.WL_F64, 8))
+    out = None
+    if rank == 0:
+        step_ms = ms / args.steps
+        out = {
+            "metric": METRIC, "value": total_bytes / (ms / 1e3) / 1e9, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "dtype_outer": "f64", "data": "synthetic",
+            "config": {"workload": "uneven batch of 16 lattices from {8^4, 12^3x24, 16^3x32, "
+                                   "16^4}, 1-8 Gaussian RHS each, kappa in [0.11, 0.124], Haar "
+                                   "links; one persistent FP32 hopping kernel per operator, "
+                                   "FP64 refinement to 1e-10",
+                       "lattices": [list(m.dims) for m in spec], "nrhs": nr,
+                       "kappa": [round(m.kappa, 5) for m in spec], "seed": 5005,
+                       "l2": "batch links total 0.5 GB FP32: larger than L2"},
+            "clocks": clocks, "gpu_launches": launches, "roofline": None,
+            "solve": {"batch_ms": step_ms, "per_lattice_mixed_ms": seq_mixed_ms,
+                      "per_lattice_fp64_ms": seq_fp64_ms,
+                      "speedup_vs_per_lattice_fp64": seq_fp64_ms / step_ms,
+                      "speedup_vs_per_lattice_mixed": seq_mixed_ms / step_ms,
+                      "max_iters": max(i["iters"] for i in infos),
+                      "max_true_resid": max(i["true_resid"] for i in infos),
+                      "systems": len(infos)},
+            "cpu_baseline": None,
+        }
+    for g in gs:
+        g.close()
     return out
 
 
@@ -444,6 +569,8 @@ def main(argv=None):
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world, local)
+    elif args.workload == BATCH_INDEX:
+        out = run_batch(args, rank, world, local)
     else:
         out = run_ours(args, rank, world, local)
     if out is not None and rank == 0:

@@ -48,10 +48,16 @@
 extern "C" {
 #endif
 
-typedef enum { WL_F64 = 0, WL_F32 = 1, WL_F16 = 2 } wl_prec;
+/* Storage precisions.  WL_DF64 stores each real as an unevaluated sum of two
+ * FP32 numbers (hi + lo, a 48-bit significand) in FP64-sized fields and
+ * computes with FP32 instructions (~2^-44 relative rounding per operation);
+ * mixed-precision solves use it for their intermediate outer residuals,
+ * because GB300 executes FP32 many times faster than FP64.  The final
+ * convergence check of every solve is IEEE FP64. */
+typedef enum { WL_F64 = 0, WL_F32 = 1, WL_F16 = 2, WL_DF64 = 3 } wl_prec;
 
 #define WL_PREC_MASK(p) (1 << (p))
-#define WL_PREC_ALL 7
+#define WL_PREC_ALL 15
 
 enum {
     WL_OK = 0,
@@ -77,7 +83,8 @@ typedef struct wl_gauge_s* wl_gauge;
 /* Create a gauge object from the canonical FP64 gauge field U (device memory,
  * V*4*9 complex, Sec. 2 "link variable").  prec_mask selects which internal
  * link copies to build (WL_PREC_MASK(WL_F32) | ...); FP64 links are always
- * built because the outer residual of every solve is FP64.  Returns
+ * built because the final residual of every solve is FP64, and df64 links
+ * whenever FP32 or FP16 is requested (the outer corrections use them).  Returns
  * WL_ERR_ARG for odd or small extents, |phi| != 1 or a NULL pointer.  U is
  * only read during the call (stream-ordered) and may be freed afterwards. */
 int wl_gauge_create(wl_gauge* g, const wl_lattice* lat, const double* U, int prec_mask,
@@ -117,10 +124,42 @@ int wilson_dslash(wl_gauge g, void* out, const void* in, int out_parity, int dag
  *   eo = 0: out = D in on full-lattice internal fields (Eq. 1; 1368 flop/site);
  *   eo = 1: out = M_ee in = in - kappa^2 H_eo H_oe in on even half fields
  *           (the Schur complement of D on the even sites).
- * dagger = 1 applies D^dag / M_ee^dag.  `out` and `in` must not overlap.
- * eo = 1 uses an odd-parity temporary from the gauge object's workspace. */
+ * With a clover term attached (wl_clover_set), D is D_clov of Eq. 2 and
+ *   eo = 0: out_p = A_pp in_p - kappa H_{p,1-p} in_{1-p},  A = 1 + F;
+ *   eo = 1: out = M_ee in = A_ee in - kappa^2 H_eo A_oo^-1 H_oe in.
+ * dagger = 1 applies D^dag / M_ee^dag (F is Hermitian, so A is unchanged).
+ * `out` and `in` must not overlap.  eo = 1 uses an odd-parity temporary from
+ * the gauge object's workspace. */
 int wilson_mult(wl_gauge g, void* out, const void* in, int eo, int dagger, wl_prec prec,
                 int nrhs, void* stream);
+
+/* Clover term (Eq. 2, Sec. 2 "Clover Fermion Matrix"):
+ *     D_clov(x,y) = D(x,y) + F(x) delta_{x,y},
+ * F(x) a 12x12 Hermitian matrix, block diagonal in the chiral basis with two
+ * 6x6 Hermitian blocks: block b acts on spins {2b, 2b+1}.  The paper takes F
+ * as given (its construction is outside the cost model); so does the library.
+ *
+ * wl_clover_set attaches F to the gauge object: from then on wilson_mult,
+ * wilson_solve and wilson_solve_batch use D_clov; wilson_dslash stays the
+ * hopping term.  F is device memory, FP64, F[V][2][6][6] complex (re, im
+ * interleaved; row/column index = local spin * 3 + colour, local spin =
+ * spin - 2b), canonical site order.  F must be Hermitian: an input whose
+ * blocks depart from it by more than 1e-10 of their largest entry returns
+ * WL_ERR_ARG, as does a site where A = 1 + F is singular (pivot below 1e-13
+ * of the block's largest entry) or, for a gauge object holding FP16, an entry
+ * of A or A^-1 beyond 6e4.  The library computes A and A^-1 per site in FP64
+ * and keeps both for each parity in every precision the gauge object holds
+ * (72 reals per site each: 576 B FP64/df64, 288 B FP32, 144 B FP16).  Returns
+ * after the set-up has finished (F may be freed).  F = NULL detaches the term.
+ * On error no clover term is attached. */
+int wl_clover_set(wl_gauge g, const double* F, void* stream);
+
+/* Site-diagonal part of D_clov on half fields of parity `parity`:
+ *     out = A in (inverse = 0)   or   out = A^-1 in (inverse = 1),
+ * nrhs fields back to back.  WL_ERR_STATE without a clover term.  `out` may
+ * equal `in`.  Asynchronous. */
+int wl_clover_apply(wl_gauge g, void* out, const void* in, int parity, int inverse,
+                    wl_prec prec, int nrhs, void* stream);
 
 /* Per-right-hand-side complex dot products and norms of internal half
  * fields (the global reductions of BiCGStab, Sec. 2):
@@ -177,8 +216,10 @@ typedef struct {
     double secs;        /* wall time of the whole call */
 } wl_solve_info;
 
-/* Solve D x_r = b_r for nrhs right-hand sides (canonical FP64, nrhs*V*12
- * complex each).  x and b may be device or host memory (host buffers are
+/* Solve D x_r = b_r (D_clov with a clover term attached; its even-odd system
+ * is A_ee - kappa^2 H_eo A_oo^-1 H_oe with b' = b_e + kappa H_eo A_oo^-1 b_o
+ * and x_o = A_oo^-1 (b_o + kappa H_oe x_e)) for nrhs right-hand sides
+ * (canonical FP64, nrhs*V*12 complex each).  x and b may be device or host memory (host buffers are
  * staged through the gauge object's workspace).  info has nrhs entries.
  * Returns WL_OK when every right-hand side reached tol, else the first
  * failing status; x always holds the best iterate. */

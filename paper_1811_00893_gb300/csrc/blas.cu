@@ -6,9 +6,56 @@
 // A vector is `nhalf` half fields per right-hand side stored back to back;
 // element j (one site) lives in half j / Vh at index j % Vh.  Each kernel
 // runs one thread per site and right-hand side (grid.y = rhs).
+#include <algorithm>
+#include <map>
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace wl {
+
+int resident_grid(const void* kernel, int block, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void*, long long>, int> cache;
+    const auto key = std::make_pair(kernel, (long long)block * (1LL << 32) + (long long)smem);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int per_sm = 0, dev = 0, sms = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess)
+        per_sm = 1;
+    cudaGetLastError();
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (per_sm > 0 ? per_sm : 1) * sms;
+    cache[key] = grid;
+    return grid;
+}
+
+__global__ void __launch_bounds__(256) finish_slots_kernel(const double* partial, long long stride,
+                                                           int nblocks, double* out, int out_stride,
+                                                           const int* active, int active_stride)
+{
+    const int slot = blockIdx.x;
+    if (active && !active[(long long)slot * active_stride]) return;
+    __shared__ double sh[3 * 32];
+    double v[3];
+    sum_partials<3>(partial + slot * stride, nblocks, v);
+    block_sum<3>(v, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) out[(long long)slot * out_stride + k] = v[k];
+}
+
+int launch_finish_slots(const double* partial, long long stride, int nblocks, int nslots,
+                        double* out, int out_stride, const int* active, int active_stride,
+                        cudaStream_t s)
+{
+    finish_slots_kernel<<<nslots, 256, 0, s>>>(partial, stride, nblocks, out, out_stride, active,
+                                                active_stride);
+    WL_CHECK_LAUNCH(0.0);
+    return WL_OK;
+}
 
 struct Vec {
     long long Vh;
@@ -32,9 +79,9 @@ __global__ void __launch_bounds__(256) cdot_kernel(const void* a, const void* b,
     using T = typename Prec<P>::real;
     const int rhs = blockIdx.y;
     if (mask && !mask[rhs]) return;
-    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double part[3] = {0, 0, 0};
-    if (j < v.nhalf * v.Vh) {
+    double part[3] = {0, 0, 0};  // per-site FP64 accumulation (off the hot path)
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < v.nhalf * v.Vh;
+         j += (long long)gridDim.x * blockDim.x) {
         long long i;
         cx<T> x[12], y[12];
         load_spinor<P>(x, at(a, v, rhs, j, i), v.Vh, i);
@@ -46,9 +93,9 @@ __global__ void __launch_bounds__(256) cdot_kernel(const void* a, const void* b,
             ci = fma(x[c].re, y[c].im, fma(-x[c].im, y[c].re, ci));
             nn = fma(y[c].re, y[c].re, fma(y[c].im, y[c].im, nn));
         }
-        part[0] = cr;
-        part[1] = ci;
-        part[2] = nn;
+        part[0] += (double)cr;
+        part[1] += (double)ci;
+        part[2] += (double)nn;
     }
     __shared__ double sh[3 * 32];
     block_sum<3>(part, sh);
@@ -92,9 +139,11 @@ __global__ void zero_kernel(void* dst, Vec v, const int* mask)
     store_spinor<P>((void*)at(dst, v, rhs, j, i), v.Vh, i, y);
 }
 
-template <int PL>
-__global__ void accum_hi_kernel(double* xhi, Vec vh, const void* xlo, Vec vl, const int* mask)
+// x_hi (FP64 or df64) += x_lo
+template <int PH, int PL>
+__global__ void accum_hi_kernel(void* xhi, Vec vh, const void* xlo, Vec vl, const int* mask)
 {
+    using TH = typename Prec<PH>::real;
     const int rhs = blockIdx.y;
     if (mask && !mask[rhs]) return;
     const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -102,12 +151,12 @@ __global__ void accum_hi_kernel(double* xhi, Vec vh, const void* xlo, Vec vl, co
     long long i;
     cx<typename Prec<PL>::real> x[12];
     load_spinor<PL>(x, at(xlo, vl, rhs, j, i), vl.Vh, i);
-    cx<double> y[12];
+    cx<TH> y[12];
     char* ph = (char*)at(xhi, vh, rhs, j, i);
-    load_spinor<WL_F64>(y, ph, vh.Vh, i);
+    load_spinor<PH>(y, ph, vh.Vh, i);
 #pragma unroll
-    for (int c = 0; c < 12; ++c) y[c] = {y[c].re + (double)x[c].re, y[c].im + (double)x[c].im};
-    store_spinor<WL_F64>(ph, vh.Vh, i, y);
+    for (int c = 0; c < 12; ++c) y[c] = {y[c].re + (TH)x[c].re, y[c].im + (TH)x[c].im};
+    store_spinor<PH>(ph, vh.Vh, i, y);
 }
 
 static Vec make_vec(wl_gauge g, int prec, int nhalf, long long rs = 0)
@@ -130,12 +179,18 @@ static dim3 blas_grid(wl_gauge g, int nhalf, int nrhs)
 int launch_cdot(wl_gauge g, int prec, const void* a, const void* b, int nhalf, int nrhs,
                 double* out, int out_stride, const int* mask, cudaStream_t s, long long rs)
 {
-    const dim3 grid = blas_grid(g, nhalf, nrhs);
+    dim3 grid = blas_grid(g, nhalf, nrhs);
+    const void* kern = prec == WL_F64 ? (const void*)cdot_kernel<WL_F64>
+                       : prec == WL_F32 ? (const void*)cdot_kernel<WL_F32>
+                       : prec == WL_F16 ? (const void*)cdot_kernel<WL_F16>
+                                        : (const void*)cdot_kernel<WL_DF64>;
+    grid.x = std::min(grid.x, (unsigned)resident_grid(kern, kBlasBlock, 0));
     WL_TRY(ensure_red(g, nrhs, grid.x));
     const Vec v = make_vec(g, prec, nhalf, rs);
     if (prec == WL_F64) cdot_kernel<WL_F64><<<grid, kBlasBlock, 0, s>>>(a, b, v, out, out_stride, mask, g->red);
     else if (prec == WL_F32) cdot_kernel<WL_F32><<<grid, kBlasBlock, 0, s>>>(a, b, v, out, out_stride, mask, g->red);
-    else cdot_kernel<WL_F16><<<grid, kBlasBlock, 0, s>>>(a, b, v, out, out_stride, mask, g->red);
+    else if (prec == WL_F16) cdot_kernel<WL_F16><<<grid, kBlasBlock, 0, s>>>(a, b, v, out, out_stride, mask, g->red);
+    else cdot_kernel<WL_DF64><<<grid, kBlasBlock, 0, s>>>(a, b, v, out, out_stride, mask, g->red);
     WL_CHECK_LAUNCH(2.0 * v.hb * nhalf * nrhs);
     return WL_OK;
 }
@@ -146,7 +201,8 @@ static void convert_from(int psrc, void* dst, Vec vd, const void* src, Vec vs, d
 {
     if (psrc == WL_F64) convert_kernel<PD, WL_F64><<<grid, kBlasBlock, 0, s>>>(dst, vd, src, vs, mask);
     else if (psrc == WL_F32) convert_kernel<PD, WL_F32><<<grid, kBlasBlock, 0, s>>>(dst, vd, src, vs, mask);
-    else convert_kernel<PD, WL_F16><<<grid, kBlasBlock, 0, s>>>(dst, vd, src, vs, mask);
+    else if (psrc == WL_F16) convert_kernel<PD, WL_F16><<<grid, kBlasBlock, 0, s>>>(dst, vd, src, vs, mask);
+    else convert_kernel<PD, WL_DF64><<<grid, kBlasBlock, 0, s>>>(dst, vd, src, vs, mask);
 }
 
 int launch_convert(wl_gauge g, int pdst, void* dst, int psrc, const void* src, int nhalf, int nrhs,
@@ -156,7 +212,8 @@ int launch_convert(wl_gauge g, int pdst, void* dst, int psrc, const void* src, i
     const Vec vd = make_vec(g, pdst, nhalf, dst_rs), vs = make_vec(g, psrc, nhalf, src_rs);
     if (pdst == WL_F64) convert_from<WL_F64>(psrc, dst, vd, src, vs, grid, mask, s);
     else if (pdst == WL_F32) convert_from<WL_F32>(psrc, dst, vd, src, vs, grid, mask, s);
-    else convert_from<WL_F16>(psrc, dst, vd, src, vs, grid, mask, s);
+    else if (pdst == WL_F16) convert_from<WL_F16>(psrc, dst, vd, src, vs, grid, mask, s);
+    else convert_from<WL_DF64>(psrc, dst, vd, src, vs, grid, mask, s);
     WL_CHECK_LAUNCH((double)(vd.hb + vs.hb) * nhalf * nrhs);
     return WL_OK;
 }
@@ -168,19 +225,28 @@ int launch_zero(wl_gauge g, int prec, void* dst, int nhalf, int nrhs, const int*
     const Vec v = make_vec(g, prec, nhalf);
     if (prec == WL_F64) zero_kernel<WL_F64><<<grid, kBlasBlock, 0, s>>>(dst, v, mask);
     else if (prec == WL_F32) zero_kernel<WL_F32><<<grid, kBlasBlock, 0, s>>>(dst, v, mask);
-    else zero_kernel<WL_F16><<<grid, kBlasBlock, 0, s>>>(dst, v, mask);
+    else if (prec == WL_F16) zero_kernel<WL_F16><<<grid, kBlasBlock, 0, s>>>(dst, v, mask);
+    else zero_kernel<WL_DF64><<<grid, kBlasBlock, 0, s>>>(dst, v, mask);
     WL_CHECK_LAUNCH((double)v.hb * nhalf * nrhs);
     return WL_OK;
 }
 
-int launch_accum_hi(wl_gauge g, double* xhi, int plo, const void* xlo, int nhalf, int nrhs,
+template <int PH>
+static void accum_from(int plo, void* xhi, Vec vh, const void* xlo, Vec vl, dim3 grid,
+                       const int* mask, cudaStream_t s)
+{
+    if (plo == WL_F64) accum_hi_kernel<PH, WL_F64><<<grid, kBlasBlock, 0, s>>>(xhi, vh, xlo, vl, mask);
+    else if (plo == WL_F32) accum_hi_kernel<PH, WL_F32><<<grid, kBlasBlock, 0, s>>>(xhi, vh, xlo, vl, mask);
+    else accum_hi_kernel<PH, WL_F16><<<grid, kBlasBlock, 0, s>>>(xhi, vh, xlo, vl, mask);
+}
+
+int launch_accum_hi(wl_gauge g, int phi, void* xhi, int plo, const void* xlo, int nhalf, int nrhs,
                     const int* mask, cudaStream_t s, long long hi_rs)
 {
     const dim3 grid = blas_grid(g, nhalf, nrhs);
-    const Vec vh = make_vec(g, WL_F64, nhalf, hi_rs), vl = make_vec(g, plo, nhalf);
-    if (plo == WL_F64) accum_hi_kernel<WL_F64><<<grid, kBlasBlock, 0, s>>>(xhi, vh, xlo, vl, mask);
-    else if (plo == WL_F32) accum_hi_kernel<WL_F32><<<grid, kBlasBlock, 0, s>>>(xhi, vh, xlo, vl, mask);
-    else accum_hi_kernel<WL_F16><<<grid, kBlasBlock, 0, s>>>(xhi, vh, xlo, vl, mask);
+    const Vec vh = make_vec(g, phi, nhalf, hi_rs), vl = make_vec(g, plo, nhalf);
+    if (phi == WL_DF64) accum_from<WL_DF64>(plo, xhi, vh, xlo, vl, grid, mask, s);
+    else accum_from<WL_F64>(plo, xhi, vh, xlo, vl, grid, mask, s);
     WL_CHECK_LAUNCH((double)(2 * vh.hb + vl.hb) * nhalf * nrhs);
     return WL_OK;
 }
@@ -192,9 +258,10 @@ using namespace wl;
 extern "C" int wl_cdot(wl_gauge g, double* out, const void* a, const void* b, wl_prec prec, int nrhs,
                        void* stream)
 {
+    WL_ENTRY();
     if (!g) return set_error(WL_ERR_ARG, "NULL gauge object");
     if (!out || !a || !b) return set_error(WL_ERR_ARG, "NULL pointer");
-    if (prec < WL_F64 || prec > WL_F16) return set_error(WL_ERR_ARG, "unknown precision");
+    if (prec < WL_F64 || prec > WL_DF64) return set_error(WL_ERR_ARG, "unknown precision");
     if (nrhs < 1 || nrhs > 65535) return set_error(WL_ERR_ARG, "nrhs must be in 1..65535");
     return launch_cdot(g, prec, a, b, 1, nrhs, out, 3, nullptr, (cudaStream_t)stream);
 }

@@ -10,6 +10,7 @@
 #include <atomic>
 #include <string>
 
+#include "df64.cuh"
 #include "wilson.h"
 
 // ---------------------------------------------------------------------------
@@ -30,13 +31,21 @@ inline void count_launch(long long n = 1, double bytes = 0.0)
 
 }  // namespace wl
 
+// A failed runtime call is reported and its (non-sticky) error consumed, so it
+// cannot resurface in a later launch check.
 #define WL_CUDA(call)                                                                     \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess)                                                            \
+        if (e_ != cudaSuccess) {                                                          \
+            cudaGetLastError();                                                           \
             return wl::set_error(WL_ERR_CUDA, std::string(#call) + ": " +                 \
                                                   cudaGetErrorString(e_));                \
+        }                                                                                 \
     } while (0)
+
+// Entry points start from a clean error state: an earlier failure elsewhere in
+// the process must not be reported as this call's launch error.
+#define WL_ENTRY() cudaGetLastError()
 
 // Check a kernel launch and account for it with its algorithmic bytes.
 #define WL_CHECK_LAUNCH(bytes)                                                            \
@@ -128,14 +137,21 @@ struct Prec<WL_F16> {
     static constexpr size_t spinor_bytes = 52;
     static constexpr size_t link_bytes = 8 * (32 + 4);
 };
+template <>
+struct Prec<WL_DF64> {
+    using real = df64;
+    static constexpr size_t spinor_bytes = 192;
+    static constexpr size_t link_bytes = 8 * 9 * 16;
+};
 
 inline size_t spinor_field_bytes(int prec, long long Vh)
 {
-    return (prec == WL_F64 ? 192 : prec == WL_F32 ? 96 : 52) * (size_t)Vh;
+    return (prec == WL_F64 || prec == WL_DF64 ? 192 : prec == WL_F32 ? 96 : 52) * (size_t)Vh;
 }
 inline size_t link_field_bytes(int prec, long long Vh)
 {
-    return (prec == WL_F64 ? 8 * 9 * 16 : prec == WL_F32 ? 8 * 72 : 8 * 36) * (size_t)Vh;
+    return (prec == WL_F64 || prec == WL_DF64 ? 8 * 9 * 16 : prec == WL_F32 ? 8 * 72 : 8 * 36) *
+           (size_t)Vh;
 }
 
 // --- spinor loads/stores --------------------------------------------------
@@ -189,6 +205,27 @@ __device__ __forceinline__ void store_spinor<WL_F32>(void* base, long long Vh, l
         p[k * Vh + i] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
 }
 
+template <>
+__device__ __forceinline__ void load_spinor<WL_DF64>(cx<df64> (&v)[12], const void* base,
+                                                     long long Vh, long long i)
+{
+    const float4* p = (const float4*)base;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        float4 t = p[c * Vh + i];
+        v[c] = {df64(t.x, t.y), df64(t.z, t.w)};
+    }
+}
+template <>
+__device__ __forceinline__ void store_spinor<WL_DF64>(void* base, long long Vh, long long i,
+                                                      const cx<df64> (&v)[12])
+{
+    float4* p = (float4*)base;
+#pragma unroll
+    for (int c = 0; c < 12; ++c)
+        p[c * Vh + i] = make_float4(v[c].re.hi, v[c].re.lo, v[c].im.hi, v[c].im.lo);
+}
+
 __device__ __forceinline__ float2 h2f(unsigned u)
 {
     __half2 h = *reinterpret_cast<__half2*>(&u);
@@ -237,6 +274,65 @@ __device__ __forceinline__ void store_spinor<WL_F16>(void* base, long long Vh, l
     ((float*)(p + 3 * Vh))[i] = m;
 }
 
+// Read-only variants for fields that no thread of the launch writes (the
+// hopping kernels' neighbour spinors): loads go through the non-coherent
+// read-only path, whose caching serves the stencil's neighbour reuse.
+template <int P>
+__device__ __forceinline__ void load_spinor_ro(cx<typename Prec<P>::real> (&v)[12],
+                                               const void* base, long long Vh, long long i);
+
+template <>
+__device__ __forceinline__ void load_spinor_ro<WL_F64>(cx<double> (&v)[12], const void* base,
+                                                       long long Vh, long long i)
+{
+    const double2* p = (const double2*)base;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        double2 t = __ldg(p + c * Vh + i);
+        v[c] = {t.x, t.y};
+    }
+}
+template <>
+__device__ __forceinline__ void load_spinor_ro<WL_F32>(cx<float> (&v)[12], const void* base,
+                                                       long long Vh, long long i)
+{
+    const float4* p = (const float4*)base;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        float4 t = __ldg(p + k * Vh + i);
+        v[2 * k] = {t.x, t.y};
+        v[2 * k + 1] = {t.z, t.w};
+    }
+}
+template <>
+__device__ __forceinline__ void load_spinor_ro<WL_F16>(cx<float> (&v)[12], const void* base,
+                                                       long long Vh, long long i)
+{
+    const uint4* p = (const uint4*)base;
+    const float nrm = __ldg((const float*)(p + 3 * Vh) + i);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        uint4 t = __ldg(p + k * Vh + i);
+        float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), d = h2f(t.w);
+        v[4 * k + 0] = {a.x * nrm, a.y * nrm};
+        v[4 * k + 1] = {b.x * nrm, b.y * nrm};
+        v[4 * k + 2] = {c.x * nrm, c.y * nrm};
+        v[4 * k + 3] = {d.x * nrm, d.y * nrm};
+    }
+}
+
+template <>
+__device__ __forceinline__ void load_spinor_ro<WL_DF64>(cx<df64> (&v)[12], const void* base,
+                                                        long long Vh, long long i)
+{
+    const float4* p = (const float4*)base;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        float4 t = __ldg(p + c * Vh + i);
+        v[c] = {df64(t.x, t.y), df64(t.z, t.w)};
+    }
+}
+
 // --- link loads -----------------------------------------------------------
 
 template <int P>
@@ -270,6 +366,17 @@ __device__ __forceinline__ void load_link<WL_F32>(cx<float> (&w)[9], const void*
     w[8] = {t.x, t.y};
 }
 template <>
+__device__ __forceinline__ void load_link<WL_DF64>(cx<df64> (&w)[9], const void* base,
+                                                   long long Vh, int d, long long i)
+{
+    const float4* p = (const float4*)base + (long long)d * 9 * Vh;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        float4 t = p[k * Vh + i];
+        w[k] = {df64(t.x, t.y), df64(t.z, t.w)};
+    }
+}
+template <>
 __device__ __forceinline__ void load_link<WL_F16>(cx<float> (&w)[9], const void* base,
                                                   long long Vh, int d, long long i)
 {
@@ -294,8 +401,19 @@ __device__ __forceinline__ void load_link<WL_F16>(cx<float> (&w)[9], const void*
 // order, so results do not depend on block scheduling.
 // ---------------------------------------------------------------------------
 
-template <int N>
-__device__ __forceinline__ void warp_sum(double (&v)[N])
+// Type in which per-warp partial sums are shuffled: FP32 for FP32 arithmetic,
+// FP64 for the wider types.
+template <typename T>
+struct RedType {
+    using type = double;
+};
+template <>
+struct RedType<float> {
+    using type = float;
+};
+
+template <int N, typename T>
+__device__ __forceinline__ void warp_sum(T (&v)[N])
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
@@ -320,6 +438,31 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double* sh)
         for (int k = 0; k < N; ++k) v[k] = lane < nw ? sh[k * 32 + lane] : 0.0;
         warp_sum<N>(v);
     }
+}
+
+// This thread's share of the sum of nblocks partial N-tuples (stride N),
+// four independent loads in flight so the loop is not one L2 latency per step.
+template <int N>
+__device__ __forceinline__ void sum_partials(const double* part, int nblocks, double (&v)[N],
+                                             long long tstride = N)
+{
+    double a[4][N];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < N; ++k) a[u][k] = 0.0;
+    const int step = blockDim.x;
+    int b = threadIdx.x;
+    for (; b + 3 * step < nblocks; b += 4 * step)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < N; ++k) a[u][k] += __ldcg(&part[(long long)(b + u * step) * tstride + k]);
+    for (; b < nblocks; b += step)
+#pragma unroll
+        for (int k = 0; k < N; ++k) a[0][k] += __ldcg(&part[(long long)b * tstride + k]);
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = (a[0][k] + a[1][k]) + (a[2][k] + a[3][k]);
 }
 
 // Scratch for grid reductions: partial[slot][block][N] and one ticket per slot.
@@ -349,11 +492,7 @@ __device__ __forceinline__ bool grid_sum(const double (&blk)[N], double (&tot)[N
     if (!last) return false;
     __threadfence();
     double v[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-#pragma unroll
-        for (int k = 0; k < N; ++k) v[k] += __ldcg(&part[(long long)b * N + k]);
+    sum_partials<N>(part, nblocks, v);
     block_sum<N>(v, sh);
     if (threadIdx.x == 0) {
 #pragma unroll

@@ -1,338 +1,22 @@
-// The even-odd hopping term of the Wilson matrix (Eq. 1) on sm_103a.
-//
-// One thread per output site of one parity.  The eight neighbour spinors are
-// spin-projected to half spinors (12 reals), multiplied by the link (folded
-// with the boundary phase, backward links pre-daggered at set-up) and
-// reconstructed into the four spin components.  Spinors and links live in
-// structure-of-arrays planes, so consecutive threads read consecutive 16-byte
-// words; the neighbour spinors' eightfold reuse is served by L1/L2 (the y, z,
-// t neighbours are the same half index shifted by a row, plane or slab).
-// The epilogue optionally forms out = x1 + b1*x2 + a*H in and accumulates
-// the complex dot (w, out) and ||out||^2 into a deterministic grid reduction,
-// so the solver's matrix applies carry their reductions for free.
-#include "internal.cuh"
+// Host side of the hopping term: launch shapes, the autotuner, right-hand-side
+// chunking and the C entry points wilson_dslash / wilson_mult.  The kernels
+// are in hop_kernels.cuh.  The epilogue optionally forms
+// out = x1 + b1*x2 + a*H in (with the clover term of Eq. 2 folded in) and
+// accumulates the complex dot (w, out) and ||out||^2 into a deterministic
+// grid reduction, so the solver's matrix applies carry their reductions for
+// free.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "hop_kernels.cuh"
 
 namespace wl {
 
-// (1 + S gamma_mu) projection / reconstruction in the chiral basis
-// (gamma_5 = diag(1,1,-1,-1)); S = -1 is Eq. 1's forward projector
-// (1 - gamma_mu), S = +1 the backward one.  With u0 = W h0, u1 = W h1 the
-// four spin rows of (1 + S gamma_mu) W psi are (u0, u1, r2, r3):
-//   mu=x: h0 = psi0 + S i psi3, h1 = psi1 + S i psi2, r2 = -S i u1, r3 = -S i u0
-//   mu=y: h0 = psi0 - S psi3,   h1 = psi1 + S psi2,   r2 =  S u1,   r3 = -S u0
-//   mu=z: h0 = psi0 + S i psi2, h1 = psi1 - S i psi3, r2 = -S i u0, r3 =  S i u1
-//   mu=t: h0 = psi0 + S psi2,   h1 = psi1 + S psi3,   r2 =  S u0,   r3 =  S u1
-template <int MU, int S, typename T>
-__device__ __forceinline__ void accumulate(cx<T> (&acc)[12], const cx<T> (&q)[12],
-                                           const cx<T> (&W)[9])
-{
-    const T s = (T)S;
-    cx<T> h0[3], h1[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const cx<T> p0 = q[c], p1 = q[3 + c], p2 = q[6 + c], p3 = q[9 + c];
-        if (MU == 0) {
-            h0[c] = p0 + s * mul_i(p3);
-            h1[c] = p1 + s * mul_i(p2);
-        } else if (MU == 1) {
-            h0[c] = p0 - s * p3;
-            h1[c] = p1 + s * p2;
-        } else if (MU == 2) {
-            h0[c] = p0 + s * mul_i(p2);
-            h1[c] = p1 - s * mul_i(p3);
-        } else {
-            h0[c] = p0 + s * p2;
-            h1[c] = p1 + s * p3;
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        cx<T> u0 = W[3 * a] * h0[0];
-        cmac(u0, W[3 * a + 1], h0[1]);
-        cmac(u0, W[3 * a + 2], h0[2]);
-        cx<T> u1 = W[3 * a] * h1[0];
-        cmac(u1, W[3 * a + 1], h1[1]);
-        cmac(u1, W[3 * a + 2], h1[2]);
-        acc[a] = acc[a] + u0;
-        acc[3 + a] = acc[3 + a] + u1;
-        if (MU == 0) {
-            acc[6 + a] = acc[6 + a] - s * mul_i(u1);
-            acc[9 + a] = acc[9 + a] - s * mul_i(u0);
-        } else if (MU == 1) {
-            acc[6 + a] = acc[6 + a] + s * u1;
-            acc[9 + a] = acc[9 + a] - s * u0;
-        } else if (MU == 2) {
-            acc[6 + a] = acc[6 + a] - s * mul_i(u0);
-            acc[9 + a] = acc[9 + a] + s * mul_i(u1);
-        } else {
-            acc[6 + a] = acc[6 + a] + s * u0;
-            acc[9 + a] = acc[9 + a] + s * u1;
-        }
-    }
-}
-
-// Half indices of the eight neighbours (order +x, -x, +y, -y, +z, -z, +t, -t)
-// of output site i on parity p, with periodic wrap-around.
-__device__ __forceinline__ void neighbours(const Geom& g, int p, int i, int (&nb)[8])
-{
-    const int xh = i % g.Lxh;
-    int r = i / g.Lxh;
-    const int y = r % g.L[1];
-    r /= g.L[1];
-    const int z = r % g.L[2];
-    const int t = r / g.L[2];
-    const int x = 2 * xh + ((p + y + z + t) & 1);
-    const int row = i - xh;
-    const int sy = (int)g.sy, sz = (int)g.sz, st = (int)g.st;
-    nb[0] = row + ((x + 1 == g.L[0] ? 0 : x + 1) >> 1);
-    nb[1] = row + ((x == 0 ? g.L[0] - 1 : x - 1) >> 1);
-    nb[2] = (y == g.L[1] - 1) ? i - (g.L[1] - 1) * sy : i + sy;
-    nb[3] = (y == 0) ? i + (g.L[1] - 1) * sy : i - sy;
-    nb[4] = (z == g.L[2] - 1) ? i - (g.L[2] - 1) * sz : i + sz;
-    nb[5] = (z == 0) ? i + (g.L[2] - 1) * sz : i - sz;
-    nb[6] = (t == g.L[3] - 1) ? i - (g.L[3] - 1) * st : i + st;
-    nb[7] = (t == 0) ? i + (g.L[3] - 1) * st : i - st;
-}
-
-template <int P, int D, int MU, int S>
-__device__ __forceinline__ void hop_one(cx<typename Prec<P>::real> (&acc)[12], const void* in,
-                                        long long Vh, int nb, const void* links, long long lVh,
-                                        int li)
-{
-    using T = typename Prec<P>::real;
-    cx<T> q[12], W[9];
-    load_spinor<P>(q, in, Vh, nb);
-    load_link<P>(W, links, lVh, D, li);
-    accumulate<MU, S, T>(acc, q, W);
-}
-
-// acc = H_{p,1-p} in at the output site whose neighbours are nb.  The links
-// are read from planes of stride lVh at index li (the global link field, or a
-// tile of it staged in shared memory).  DAG flips the projector signs.
-template <int P, bool DAG>
-__device__ __forceinline__ void hop_site(cx<typename Prec<P>::real> (&acc)[12], const int (&nb)[8],
-                                         long long Vh, const void* in, const void* links,
-                                         long long lVh, int li)
-{
-    using T = typename Prec<P>::real;
-#pragma unroll
-    for (int c = 0; c < 12; ++c) acc[c] = {(T)0, (T)0};
-    constexpr int F = DAG ? +1 : -1;  // forward projector sign
-    constexpr int B = -F;             // backward projector sign
-    hop_one<P, 0, 0, F>(acc, in, Vh, nb[0], links, lVh, li);
-    hop_one<P, 1, 0, B>(acc, in, Vh, nb[1], links, lVh, li);
-    hop_one<P, 2, 1, F>(acc, in, Vh, nb[2], links, lVh, li);
-    hop_one<P, 3, 1, B>(acc, in, Vh, nb[3], links, lVh, li);
-    hop_one<P, 4, 2, F>(acc, in, Vh, nb[4], links, lVh, li);
-    hop_one<P, 5, 2, B>(acc, in, Vh, nb[5], links, lVh, li);
-    hop_one<P, 6, 3, F>(acc, in, Vh, nb[6], links, lVh, li);
-    hop_one<P, 7, 3, B>(acc, in, Vh, nb[7], links, lVh, li);
-}
-
-struct HopArgs {
-    Geom g;
-    const void* links[2];
-    const char* in[2];
-    char* out[2];
-    const char* x1[2];
-    const char* x2[2];
-    const char* w[2];
-    long long rs_in, rs_out, rs_x1, rs_x2, rs_w;
-    double a, b1;
-    int parity0, blocks_per_parity;
-    double* dot_out;
-    int dot_stride;
-    const int* active;
-    int active_stride;
-    RedScratch red;
-};
-
-// out = x1 + b1 x2 + a acc at site i of right-hand side rhs; with DOT the
-// thread's contributions to (w, out) and ||out||^2 go to part.
-template <int P, bool DOT>
-__device__ __forceinline__ void epilogue(cx<typename Prec<P>::real> (&acc)[12], const HopArgs& A,
-                                         int pidx, int rhs, int i, double (&part)[3])
-{
-    using T = typename Prec<P>::real;
-    const T a = (T)A.a;
-#pragma unroll
-    for (int c = 0; c < 12; ++c) acc[c] = a * acc[c];
-    if (A.x1[pidx]) {
-        cx<T> x[12];
-        load_spinor<P>(x, A.x1[pidx] + rhs * A.rs_x1, A.g.Vh, i);
-#pragma unroll
-        for (int c = 0; c < 12; ++c) acc[c] = acc[c] + x[c];
-    }
-    if (A.x2[pidx]) {
-        cx<T> x[12];
-        const T b1 = (T)A.b1;
-        load_spinor<P>(x, A.x2[pidx] + rhs * A.rs_x2, A.g.Vh, i);
-#pragma unroll
-        for (int c = 0; c < 12; ++c) acc[c] = acc[c] + b1 * x[c];
-    }
-    store_spinor<P>(A.out[pidx] + rhs * A.rs_out, A.g.Vh, i, acc);
-    if (DOT) {
-        T cr = 0, ci = 0, nn = 0;
-        if (A.w[pidx]) {
-            cx<T> w[12];
-            load_spinor<P>(w, A.w[pidx] + rhs * A.rs_w, A.g.Vh, i);
-#pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                cr = fma(w[c].re, acc[c].re, fma(w[c].im, acc[c].im, cr));
-                ci = fma(w[c].re, acc[c].im, fma(-w[c].im, acc[c].re, ci));
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < 12; ++c) nn = fma(acc[c].re, acc[c].re, fma(acc[c].im, acc[c].im, nn));
-        part[0] = cr;
-        part[1] = ci;
-        part[2] = nn;
-    }
-}
-
-// One right-hand side per grid row, one output site per thread.
-template <int P, bool DAG, bool DOT>
-__global__ void __launch_bounds__(256) hop_kernel(const HopArgs A)
-{
-    using T = typename Prec<P>::real;
-    const int rhs = blockIdx.y;
-    if (A.active && A.active[rhs * A.active_stride] == 0) return;  // uniform per block
-    const int pidx = blockIdx.x / A.blocks_per_parity;
-    const int p = A.parity0 + pidx;
-    const int i = (blockIdx.x - pidx * A.blocks_per_parity) * blockDim.x + threadIdx.x;
-    double part[3] = {0.0, 0.0, 0.0};
-    if (i < A.g.Vh) {
-        cx<T> acc[12];
-        int nb[8];
-        neighbours(A.g, p, i, nb);
-        hop_site<P, DAG>(acc, nb, A.g.Vh, A.in[pidx] + rhs * A.rs_in, A.links[pidx], A.g.Vh, i);
-        epilogue<P, DOT>(acc, A, pidx, rhs, i, part);
-    }
-    if (DOT) {
-        __shared__ double sh[3 * 32];
-        block_sum<3>(part, sh);
-        double tot[3];
-        if (grid_sum<3>(part, tot, A.red, rhs, gridDim.x, blockIdx.x, sh)) {
-            double* o = A.dot_out + (long long)rhs * A.dot_stride;
-            o[0] = tot[0];
-            o[1] = tot[1];
-            o[2] = tot[2];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Many right-hand sides: a block owns kTile output sites of one parity.  It
-// copies their links (all eight hops) into shared memory once, then its
-// warps sweep the right-hand sides, lane = site, reading the links from
-// shared memory: the links leave HBM once for all right-hand sides.
-// ---------------------------------------------------------------------------
-
-static constexpr int kTile = 32;
-static constexpr int kMaxRhsLaunch = 32;
-
-template <int P>
-struct LinkPlanes;  // the link field as 16-byte planes plus narrower planes
-template <>
-struct LinkPlanes<WL_F64> {
-    static constexpr int n16 = 72, nsmall = 0, small_bytes = 8;
-};
-template <>
-struct LinkPlanes<WL_F32> {
-    static constexpr int n16 = 32, nsmall = 8, small_bytes = 8;
-};
-template <>
-struct LinkPlanes<WL_F16> {
-    static constexpr int n16 = 16, nsmall = 8, small_bytes = 4;
-};
-
-// Copy the links of sites [base, base + n) into a kTile-stride tile.
-template <int P>
-__device__ __forceinline__ void stage_links(char* sm, const char* gl, long long Vh, int base, int n)
-{
-    using LP = LinkPlanes<P>;
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
-    for (int e = tid; e < LP::n16 * kTile; e += nt) {
-        const int q = e / kTile, j = e - q * kTile;
-        if (j < n) ((uint4*)sm)[q * kTile + j] = __ldg((const uint4*)gl + q * Vh + base + j);
-    }
-    if (LP::nsmall) {
-        const char* gs = gl + (size_t)LP::n16 * 16 * Vh;
-        char* ss = sm + LP::n16 * 16 * kTile;
-        for (int e = tid; e < LP::nsmall * kTile; e += nt) {
-            const int q = e / kTile, j = e - q * kTile;
-            if (j >= n) continue;
-            if (LP::small_bytes == 8)
-                ((uint2*)ss)[q * kTile + j] = __ldg((const uint2*)gs + q * Vh + base + j);
-            else
-                ((unsigned*)ss)[q * kTile + j] = __ldg((const unsigned*)gs + q * Vh + base + j);
-        }
-    }
-}
-
-template <int P, bool DAG, bool DOT>
-__global__ void __launch_bounds__(256) hop_mrhs_kernel(const HopArgs A, int nrhs)
-{
-    using T = typename Prec<P>::real;
-    extern __shared__ __align__(16) char smem[];
-    const int pidx = blockIdx.x / A.blocks_per_parity;
-    const int p = A.parity0 + pidx;
-    const int base = (blockIdx.x - pidx * A.blocks_per_parity) * kTile;
-    const int n = (int)min((long long)kTile, A.g.Vh - base);
-    stage_links<P>(smem, (const char*)A.links[pidx], A.g.Vh, base, n);
-    double* bpart = (double*)(smem + Prec<P>::link_bytes * kTile);
-    __syncthreads();
-    const int lane = threadIdx.x, i = base + lane;
-    const bool valid = lane < n;
-    int nb[8];
-    if (valid) neighbours(A.g, p, i, nb);
-    for (int r = threadIdx.y; r < nrhs; r += blockDim.y) {
-        const bool act = !A.active || A.active[r * A.active_stride] != 0;  // warp-uniform
-        double part[3] = {0.0, 0.0, 0.0};
-        if (act && valid) {
-            cx<T> acc[12];
-            hop_site<P, DAG>(acc, nb, A.g.Vh, A.in[pidx] + r * A.rs_in, smem, kTile, lane);
-            epilogue<P, DOT>(acc, A, pidx, r, i, part);
-        }
-        if (DOT) {
-            warp_sum<3>(part);
-            if (lane == 0)
-                for (int k = 0; k < 3; ++k) bpart[3 * r + k] = part[k];
-        }
-    }
-    if (!DOT) return;
-    // every block leaves its per-rhs partials; the last block to finish adds
-    // them up in block order (one ticket for all right-hand sides)
-    __syncthreads();
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
-    for (int e = tid; e < 3 * nrhs; e += nt) {
-        const int r = e / 3, k = e - 3 * r;
-        A.red.partial[((long long)r * A.red.max_blocks + blockIdx.x) * 3 + k] = bpart[e];
-    }
-    __threadfence();
-    __syncthreads();
-    __shared__ bool last;
-    if (tid == 0) last = atomicAdd(&A.red.ticket[0], 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    const int wid = tid >> 5, nw = nt >> 5;
-    for (int r = wid; r < nrhs; r += nw) {
-        double v[3] = {0.0, 0.0, 0.0};
-        const double* pr = A.red.partial + (long long)r * A.red.max_blocks * 3;
-        for (int b = lane; b < (int)gridDim.x; b += 32)
-            for (int k = 0; k < 3; ++k) v[k] += __ldcg(&pr[(long long)b * 3 + k]);
-        warp_sum<3>(v);
-        const bool act = !A.active || A.active[r * A.active_stride] != 0;
-        if (lane == 0 && act) {
-            double* o = A.dot_out + (long long)r * A.dot_stride;
-            o[0] = v[0];
-            o[1] = v[1];
-            o[2] = v[2];
-        }
-    }
-    if (tid == 0) A.red.ticket[0] = 0;
-}
+// the clover variants are instantiated in dslash_clover.cu
+extern template struct HopKernels<kClX2>;
+extern template struct HopKernels<kClOut>;
 
 // ---------------------------------------------------------------------------
 // host side
@@ -340,64 +24,161 @@ __global__ void __launch_bounds__(256) hop_mrhs_kernel(const HopArgs A, int nrhs
 
 static const int kHopBlock = 128;
 
-template <int P>
-static void launch_mrhs_t(const HopLaunch& h, const HopArgs& A, int nrhs, dim3 grid, dim3 block,
-                          size_t smem, cudaStream_t s)
+static void launch_single(const HopLaunch& h, const HopArgs& A, dim3 grid, int block, cudaStream_t s)
 {
-    if (h.dagger) {
-        if (h.dot) hop_mrhs_kernel<P, true, true><<<grid, block, smem, s>>>(A, nrhs);
-        else hop_mrhs_kernel<P, true, false><<<grid, block, smem, s>>>(A, nrhs);
-    } else {
-        if (h.dot) hop_mrhs_kernel<P, false, true><<<grid, block, smem, s>>>(A, nrhs);
-        else hop_mrhs_kernel<P, false, false><<<grid, block, smem, s>>>(A, nrhs);
+    switch (h.cl_mode) {
+        case kClX2: HopKernels<kClX2>::single(h.prec, h.dagger, h.dot, A, grid, block, s); break;
+        case kClOut: HopKernels<kClOut>::single(h.prec, h.dagger, h.dot, A, grid, block, s); break;
+        default: HopKernels<kClNone>::single(h.prec, h.dagger, h.dot, A, grid, block, s); break;
     }
 }
 
-template <int P>
-static void launch_hop_t(const HopLaunch& h, const HopArgs& A, dim3 grid, int block, cudaStream_t s)
+static void launch_multi(const HopLaunch& h, const HopArgs& A, int nrhs, dim3 grid, dim3 block,
+                         size_t smem, cudaStream_t s)
 {
-    if (h.dagger) {
-        if (h.dot) hop_kernel<P, true, true><<<grid, block, 0, s>>>(A);
-        else hop_kernel<P, true, false><<<grid, block, 0, s>>>(A);
-    } else {
-        if (h.dot) hop_kernel<P, false, true><<<grid, block, 0, s>>>(A);
-        else hop_kernel<P, false, false><<<grid, block, 0, s>>>(A);
+    switch (h.cl_mode) {
+        case kClX2: HopKernels<kClX2>::multi(h.prec, h.dagger, h.dot, A, nrhs, grid, block, smem, s); break;
+        case kClOut: HopKernels<kClOut>::multi(h.prec, h.dagger, h.dot, A, nrhs, grid, block, smem, s); break;
+        default: HopKernels<kClNone>::multi(h.prec, h.dagger, h.dot, A, nrhs, grid, block, smem, s); break;
     }
+}
+
+// Resident-block grid of the reducing single-RHS hop kernel.
+static int single_grid_cap(const HopLaunch& h, int block)
+{
+    const void* k = h.cl_mode == kClX2    ? HopKernels<kClX2>::reducing(h.prec, h.dagger)
+                    : h.cl_mode == kClOut ? HopKernels<kClOut>::reducing(h.prec, h.dagger)
+                                          : HopKernels<kClNone>::reducing(h.prec, h.dagger);
+    return resident_grid(k, block, 0);
+}
+
+// Launch one chunk of right-hand sides with launch shape `shape`: threads per
+// block for the single-RHS kernel, right-hand-side lanes (warps) per block for
+// the multi-RHS kernel.
+static int launch_shape(const HopLaunch& h, HopArgs& A, int nrhs, int shape, cudaStream_t s)
+{
+    const bool multi = nrhs > 1;
+    const int tile = multi ? kTile : shape;
+    const long long bpp = (A.g.Vh + tile - 1) / tile;
+    A.blocks_per_parity = (int)bpp;
+    A.nparity = h.nparity;
+    unsigned gx = (unsigned)(bpp * h.nparity);
+    if (!multi) {
+        if (h.dot) gx = std::min(gx, (unsigned)single_grid_cap(h, shape));
+        launch_single(h, A, dim3(gx, 1), shape, s);
+    } else {
+        const dim3 block(kTile, shape);
+        const size_t smem = link_field_bytes(h.prec, kTile) + sizeof(double) * 3 * nrhs;
+        launch_multi(h, A, nrhs, dim3(gx), block, smem, s);
+        if (h.dot)  // add the per-block partials of each right-hand side
+            return launch_finish_slots(A.red.partial, (long long)A.red.max_blocks * 3, (int)gx, nrhs,
+                                       A.dot_out, A.dot_stride, A.active, A.active_stride, s);
+    }
+    return WL_OK;
+}
+
+static bool autotune_enabled()
+{
+    static const bool on = [] {
+        const char* e = getenv("WL_AUTOTUNE");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+// Pick the launch shape for this kernel configuration: the cached choice, or
+// (first use, outside stream capture) the fastest candidate timed with CUDA
+// events on the launching stream.  Re-running a hopping launch is harmless:
+// it is out of place and its reductions are recomputed from scratch.
+static int tuned_shape(wl_gauge g, const HopLaunch& h, HopArgs& A, int nrhs, cudaStream_t s,
+                       int* shape)
+{
+    const bool multi = nrhs > 1;
+    const int dflt = multi ? (nrhs < 8 ? nrhs : 8) : kHopBlock;
+    char key[96];
+    snprintf(key, sizeof key, "hop p%d d%d dot%d np%d r%d x%d%d w%d c%d", h.prec, h.dagger, (int)h.dot,
+             h.nparity, nrhs, h.x1[0] != nullptr, h.x2[0] != nullptr, h.w[0] != nullptr, h.cl_mode);
+    auto it = g->tuned.find(key);
+    if (it != g->tuned.end()) {
+        *shape = it->second.block;
+        return WL_OK;
+    }
+    *shape = dflt;
+    if (!multi) {  // explicit override of the single-RHS block size (for sweeps)
+        const char* fb = getenv("WL_HOP_BLOCK");
+        const int v = fb ? atoi(fb) : 0;
+        if (v == 64 || v == 128 || v == 256) {
+            *shape = v;
+            return WL_OK;
+        }
+    }
+    if (!autotune_enabled() || is_capturing(s)) return WL_OK;
+    std::vector<int> cand;
+    if (multi) {
+        for (int l : {1, 2, 4, 8})
+            if (l <= nrhs) cand.push_back(l);
+    } else {
+        cand = {64, 128, 256};
+    }
+    cudaEvent_t e0, e1;
+    WL_CUDA(cudaEventCreate(&e0));
+    WL_CUDA(cudaEventCreate(&e1));
+    for (int c : cand) {  // warm every candidate once
+        WL_TRY(launch_shape(h, A, nrhs, c, s));
+        WL_CHECK_LAUNCH(0.0);
+    }
+    // interleaved rounds so that a drifting clock or cache state affects every
+    // candidate alike; each keeps its fastest round
+    std::vector<float> best_t(cand.size(), 1e30f);
+    for (int round = 0; round < 4; ++round)
+        for (size_t ci = 0; ci < cand.size(); ++ci) {
+            cudaEventRecord(e0, s);
+            WL_TRY(launch_shape(h, A, nrhs, cand[ci], s));
+            cudaEventRecord(e1, s);
+            WL_CHECK_LAUNCH(0.0);
+            WL_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best_t[ci] = std::min(best_t[ci], ms);
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    size_t bi = 0;
+    for (size_t ci = 1; ci < cand.size(); ++ci)
+        if (best_t[ci] < best_t[bi]) bi = ci;
+    const int best_shape = cand[bi];
+    if (getenv("WL_AUTOTUNE_VERBOSE")) {
+        fprintf(stderr, "[wl autotune] %s Vh=%lld:", key, g->geo.Vh);
+        for (size_t ci = 0; ci < cand.size(); ++ci) fprintf(stderr, " %d:%.1fus", cand[ci], best_t[ci] * 1e3f);
+        fprintf(stderr, " -> %d\n", best_shape);
+    }
+    Tuned tv;
+    tv.block = best_shape;
+    g->tuned[key] = tv;
+    *shape = best_shape;
+    return WL_OK;
 }
 
 static int launch_hop_chunk(wl_gauge g, const HopLaunch& h, HopArgs A, int nrhs, cudaStream_t s)
 {
     const bool multi = nrhs > 1;
-    const int tile = multi ? kTile : kHopBlock;
-    const long long bpp = (g->geo.Vh + tile - 1) / tile;
-    A.blocks_per_parity = (int)bpp;
-    const unsigned gx = (unsigned)(bpp * h.nparity);
-    if (h.dot) WL_TRY(ensure_red(g, nrhs, (long long)gx));
+    if (h.dot) {  // sized for the smallest tile any candidate shape uses
+        const long long most = ((g->geo.Vh + 31) / 32) * h.nparity;
+        WL_TRY(ensure_red(g, nrhs, most));
+    }
     A.red = g->red;
+    int shape = 0;
+    WL_TRY(tuned_shape(g, h, A, nrhs, s, &shape));
+    (void)multi;
     // algorithmic bytes: links once for all rhs; in, out and epilogue fields per rhs
+    // (and the clover matrix once, like the links)
     const int extra = (h.x1[0] ? 1 : 0) + (h.x2[0] ? 1 : 0) + (h.w[0] ? 1 : 0);
     const double bytes = (double)g->geo.Vh * h.nparity *
-                         (link_field_bytes(h.prec, 1) +
+                         (link_field_bytes(h.prec, 1) + (h.cl_mode ? clover_site_bytes(h.prec) : 0) +
                           (double)nrhs * (2 + extra) * spinor_field_bytes(h.prec, 1));
     int slot = -1;
     timing_begin(g, s, bytes, h.prec, &slot);
-    if (!multi) {
-        const dim3 grid(gx, 1);
-        switch (h.prec) {
-            case WL_F64: launch_hop_t<WL_F64>(h, A, grid, kHopBlock, s); break;
-            case WL_F32: launch_hop_t<WL_F32>(h, A, grid, kHopBlock, s); break;
-            default: launch_hop_t<WL_F16>(h, A, grid, kHopBlock, s); break;
-        }
-    } else {
-        const int lanes = nrhs < 8 ? nrhs : 8;
-        const dim3 block(kTile, lanes);
-        const size_t smem = link_field_bytes(h.prec, kTile) + sizeof(double) * 3 * nrhs;
-        switch (h.prec) {
-            case WL_F64: launch_mrhs_t<WL_F64>(h, A, nrhs, dim3(gx), block, smem, s); break;
-            case WL_F32: launch_mrhs_t<WL_F32>(h, A, nrhs, dim3(gx), block, smem, s); break;
-            default: launch_mrhs_t<WL_F16>(h, A, nrhs, dim3(gx), block, smem, s); break;
-        }
-    }
+    WL_TRY(launch_shape(h, A, nrhs, shape, s));
     WL_CHECK_LAUNCH(bytes);
     timing_end(g, s, slot);
     return WL_OK;
@@ -412,7 +193,10 @@ int launch_hop(wl_gauge g, const HopLaunch& h, cudaStream_t s)
     for (int k = 0; k < 2; ++k) {
         const int p = h.parity0 + (k < h.nparity ? k : 0);
         A.links[k] = g->links[h.prec][p];
+        A.cl[k] = h.clov[k];
     }
+    if (h.cl_mode && (!h.clov[0] || (h.nparity == 2 && !h.clov[1])))
+        return set_error(WL_ERR_STATE, "gauge object has no clover term in the requested precision");
     A.rs_in = h.rs_in;
     A.rs_out = h.rs_out;
     A.rs_x1 = h.rs_x1;
@@ -450,7 +234,7 @@ using namespace wl;
 static int check_common(wl_gauge g, const void* out, const void* in, wl_prec prec, int nrhs)
 {
     if (!g) return set_error(WL_ERR_ARG, "NULL gauge object");
-    if (prec < WL_F64 || prec > WL_F16) return set_error(WL_ERR_ARG, "unknown precision");
+    if (prec < WL_F64 || prec > WL_DF64) return set_error(WL_ERR_ARG, "unknown precision");
     if (nrhs < 1) return set_error(WL_ERR_ARG, "nrhs must be >= 1");
     if (nrhs > 65535) return set_error(WL_ERR_ARG, "nrhs must be <= 65535");
     if (!out || !in) return set_error(WL_ERR_ARG, "NULL field pointer");
@@ -465,6 +249,7 @@ static int check_common(wl_gauge g, const void* out, const void* in, wl_prec pre
 extern "C" int wilson_dslash(wl_gauge g, void* out, const void* in, int out_parity, int dagger,
                              wl_prec prec, int nrhs, void* stream)
 {
+    WL_ENTRY();
     WL_TRY(check_common(g, out, in, prec, nrhs));
     if (out_parity != 0 && out_parity != 1) return set_error(WL_ERR_ARG, "out_parity must be 0 or 1");
     const size_t fb = spinor_field_bytes(prec, g->geo.Vh);
@@ -484,6 +269,7 @@ extern "C" int wilson_dslash(wl_gauge g, void* out, const void* in, int out_pari
 extern "C" int wilson_mult(wl_gauge g, void* out, const void* in, int eo, int dagger, wl_prec prec,
                            int nrhs, void* stream)
 {
+    WL_ENTRY();
     WL_TRY(check_common(g, out, in, prec, nrhs));
     cudaStream_t s = (cudaStream_t)stream;
     const size_t fb = spinor_field_bytes(prec, g->geo.Vh);
@@ -503,13 +289,25 @@ extern "C" int wilson_mult(wl_gauge g, void* out, const void* in, int eo, int da
         h.in[1] = (const char*)in;
         h.out[0] = out;
         h.out[1] = (char*)out + fb;
-        h.x1[0] = in;
-        h.x1[1] = (const char*)in + fb;
-        h.rs_in = h.rs_out = h.rs_x1 = (long long)(2 * fb);
+        h.rs_in = h.rs_out = (long long)(2 * fb);
         h.a = -kappa;
+        if (g->has_clover) {  // out_p = A_pp in_p - kappa H in_{1-p}
+            h.x2[0] = in;
+            h.x2[1] = (const char*)in + fb;
+            h.rs_x2 = (long long)(2 * fb);
+            h.b1 = 1.0;
+            h.cl_mode = kClX2;
+            h.clov[0] = g->clov[prec][0][0];
+            h.clov[1] = g->clov[prec][1][0];
+        } else {
+            h.x1[0] = in;
+            h.x1[1] = (const char*)in + fb;
+            h.rs_x1 = (long long)(2 * fb);
+        }
         return launch_hop(g, h, s);
     }
-    // M_ee = 1 - kappa^2 H_eo H_oe on even half fields
+    // M_ee = 1 - kappa^2 H_eo H_oe on even half fields (A_ee - kappa^2 H_eo A_oo^-1 H_oe
+    // with a clover term)
     WL_TRY(ensure_tmp(g, prec, fb * nrhs));
     HopLaunch h1;
     h1.prec = prec;
@@ -520,13 +318,26 @@ extern "C" int wilson_mult(wl_gauge g, void* out, const void* in, int eo, int da
     h1.out[0] = g->tmp[prec];
     h1.rs_in = h1.rs_out = (long long)fb;
     h1.a = 1.0;
+    if (g->has_clover) {  // tmp = A_oo^-1 H_oe in
+        h1.cl_mode = kClOut;
+        h1.clov[0] = g->clov[prec][1][1];
+    }
     WL_TRY(launch_hop(g, h1, s));
     HopLaunch h2 = h1;
     h2.parity0 = 0;
     h2.in[0] = g->tmp[prec];
     h2.out[0] = out;
-    h2.x1[0] = in;
-    h2.rs_x1 = (long long)fb;
     h2.a = -kappa * kappa;
+    if (g->has_clover) {  // out = A_ee in - kappa^2 H_eo tmp
+        h2.x2[0] = in;
+        h2.rs_x2 = (long long)fb;
+        h2.b1 = 1.0;
+        h2.cl_mode = kClX2;
+        h2.clov[0] = g->clov[prec][0][0];
+    } else {
+        h2.x1[0] = in;
+        h2.rs_x1 = (long long)fb;
+        h2.cl_mode = kClNone;
+    }
     return launch_hop(g, h2, s);
 }

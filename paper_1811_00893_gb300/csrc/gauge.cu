@@ -38,16 +38,6 @@ bool is_capturing(cudaStream_t s)
     return st != cudaStreamCaptureStatusNone;
 }
 
-// Canonical site index of half index i on parity p.
-__device__ __forceinline__ long long site_of_half(const Geom& g, int p, long long i)
-{
-    const long long row = i / g.Lxh;  // (y, z, t) row
-    const int y = (int)(row % g.L[1]);
-    const int z = (int)((row / g.L[1]) % g.L[2]);
-    const int t = (int)(row / ((long long)g.L[1] * g.L[2]));
-    return 2 * i + ((p + y + z + t) & 1);
-}
-
 // ---------------------------------------------------------------------------
 // links: W_d(x) for the 8 hops of each output site, phases folded in,
 // backward links daggered.
@@ -74,6 +64,16 @@ __device__ __forceinline__ void store_link<WL_F32>(void* base, long long Vh, int
                                     (float)w[2 * k + 1].im);
     float2* q = (float2*)((float4*)base + 8 * 4 * Vh) + (long long)d * Vh;
     q[i] = make_float2((float)w[8].re, (float)w[8].im);
+}
+template <>
+__device__ __forceinline__ void store_link<WL_DF64>(void* base, long long Vh, int d, long long i,
+                                                    const cx<double> (&w)[9])
+{
+    float4* p = (float4*)base + (long long)d * 9 * Vh;
+    for (int k = 0; k < 9; ++k) {
+        const df64 re(w[k].re), im(w[k].im);
+        p[k * Vh + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
 }
 template <>
 __device__ __forceinline__ void store_link<WL_F16>(void* base, long long Vh, int d, long long i,
@@ -259,6 +259,7 @@ static int validate_lattice(const wl_lattice* lat)
 extern "C" int wl_gauge_create(wl_gauge* out, const wl_lattice* lat, const double* U, int prec_mask,
                                void* stream)
 {
+    WL_ENTRY();
     if (!out) return set_error(WL_ERR_ARG, "NULL output handle");
     *out = nullptr;
     WL_TRY(validate_lattice(lat));
@@ -277,6 +278,9 @@ extern "C" int wl_gauge_create(wl_gauge* out, const wl_lattice* lat, const doubl
         g->bc_im[k] = lat->bc_im[k];
     }
     g->prec_mask = (prec_mask & WL_PREC_ALL) | WL_PREC_MASK(WL_F64);
+    // the outer residual corrections of mixed-precision solves run in df64
+    if (g->prec_mask & (WL_PREC_MASK(WL_F32) | WL_PREC_MASK(WL_F16)))
+        g->prec_mask |= WL_PREC_MASK(WL_DF64);
     int rc = WL_OK;
     do {
         if (cudaGetDevice(&g->device) != cudaSuccess) { rc = set_error(WL_ERR_CUDA, "cudaGetDevice"); break; }
@@ -288,7 +292,7 @@ extern "C" int wl_gauge_create(wl_gauge* out, const wl_lattice* lat, const doubl
         }
         const int block = 128;
         const unsigned grid = (unsigned)((g->geo.Vh + block - 1) / block);
-        for (int prec = 0; prec < 3 && rc == WL_OK; ++prec) {
+        for (int prec = 0; prec < 4 && rc == WL_OK; ++prec) {
             if (!(g->prec_mask & WL_PREC_MASK(prec))) continue;
             for (int p = 0; p < 2; ++p) {
                 cudaError_t e = cudaMalloc(&g->links[prec][p], link_field_bytes(prec, g->geo.Vh));
@@ -298,7 +302,8 @@ extern "C" int wl_gauge_create(wl_gauge* out, const wl_lattice* lat, const doubl
                 }
                 if (prec == WL_F64) build_links_kernel<WL_F64><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, bc, p);
                 else if (prec == WL_F32) build_links_kernel<WL_F32><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, bc, p);
-                else build_links_kernel<WL_F16><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, bc, p);
+                else if (prec == WL_F16) build_links_kernel<WL_F16><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, bc, p);
+                else build_links_kernel<WL_DF64><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, bc, p);
                 e = cudaGetLastError();
                 if (e != cudaSuccess) {
                     rc = set_error(WL_ERR_CUDA, std::string("link build launch: ") + cudaGetErrorString(e));
@@ -320,13 +325,16 @@ extern "C" int wl_gauge_create(wl_gauge* out, const wl_lattice* lat, const doubl
 }
 
 void free_workspace(wl_gauge g);  // solver.cu
+void batch_forget(wl_gauge g);    // batch.cu
 
 extern "C" int wl_gauge_destroy(wl_gauge g)
 {
     if (!g) return WL_OK;
     cudaDeviceSynchronize();
+    batch_forget(g);
     free_workspace(g);
-    for (int prec = 0; prec < 3; ++prec) {
+    free_clover(g);
+    for (int prec = 0; prec < 4; ++prec) {
         for (int p = 0; p < 2; ++p)
             if (g->links[prec][p]) cudaFree(g->links[prec][p]);
         if (g->tmp[prec]) cudaFree(g->tmp[prec]);
@@ -343,7 +351,7 @@ extern "C" long long wl_half_volume(wl_gauge g) { return g ? g->geo.Vh : 0; }
 
 extern "C" size_t wl_field_bytes(wl_gauge g, wl_prec prec, int nrhs)
 {
-    if (!g || prec < WL_F64 || prec > WL_F16 || nrhs < 0) return 0;
+    if (!g || prec < WL_F64 || prec > WL_DF64 || nrhs < 0) return 0;
     return spinor_field_bytes(prec, g->geo.Vh) * (size_t)nrhs;
 }
 
@@ -352,41 +360,63 @@ static int conv_check(wl_gauge g, const void* a, const void* b, int parity, wl_p
     if (!g) return set_error(WL_ERR_ARG, "NULL gauge object");
     if (!a || !b) return set_error(WL_ERR_ARG, "NULL field pointer");
     if (parity != 0 && parity != 1) return set_error(WL_ERR_ARG, "parity must be 0 or 1");
-    if (prec < WL_F64 || prec > WL_F16) return set_error(WL_ERR_ARG, "unknown precision");
+    if (prec < WL_F64 || prec > WL_DF64) return set_error(WL_ERR_ARG, "unknown precision");
     if (nrhs < 1 || nrhs > 65535) return set_error(WL_ERR_ARG, "nrhs must be in 1..65535");
     return WL_OK;
 }
 
-extern "C" int wl_field_to_internal(wl_gauge g, void* out, const double* in, int parity, wl_prec prec,
-                                    int nrhs, void* stream)
+namespace wl {
+
+int field_to_internal(wl_gauge g, void* out, const double* in, int parity, int prec, int nrhs,
+                      cudaStream_t s)
 {
-    WL_TRY(conv_check(g, out, in, parity, prec, nrhs));
-    cudaStream_t s = (cudaStream_t)stream;
     const int block = 128;
     dim3 grid((unsigned)((g->geo.Vh + block - 1) / block), (unsigned)nrhs);
     const size_t fb = spinor_field_bytes(prec, g->geo.Vh);
     const long long V = 2 * g->geo.Vh;
-    if (prec == WL_F64) to_internal_kernel<WL_F64><<<grid, block, 0, s>>>((char*)out, in, g->geo, parity, fb, V);
-    else if (prec == WL_F32) to_internal_kernel<WL_F32><<<grid, block, 0, s>>>((char*)out, in, g->geo, parity, fb, V);
-    else to_internal_kernel<WL_F16><<<grid, block, 0, s>>>((char*)out, in, g->geo, parity, fb, V);
+    switch (prec) {
+        case WL_F64: to_internal_kernel<WL_F64><<<grid, block, 0, s>>>((char*)out, in, g->geo, parity, fb, V); break;
+        case WL_F32: to_internal_kernel<WL_F32><<<grid, block, 0, s>>>((char*)out, in, g->geo, parity, fb, V); break;
+        case WL_F16: to_internal_kernel<WL_F16><<<grid, block, 0, s>>>((char*)out, in, g->geo, parity, fb, V); break;
+        default: to_internal_kernel<WL_DF64><<<grid, block, 0, s>>>((char*)out, in, g->geo, parity, fb, V); break;
+    }
     WL_CHECK_LAUNCH((double)nrhs * g->geo.Vh * (192.0 + (double)fb / g->geo.Vh));
     return WL_OK;
+}
+
+int field_to_canonical(wl_gauge g, double* out, const void* in, int parity, int prec, int nrhs,
+                       cudaStream_t s)
+{
+    const int block = 128;
+    dim3 grid((unsigned)((g->geo.Vh + block - 1) / block), (unsigned)nrhs);
+    const size_t fb = spinor_field_bytes(prec, g->geo.Vh);
+    const long long V = 2 * g->geo.Vh;
+    switch (prec) {
+        case WL_F64: to_canonical_kernel<WL_F64><<<grid, block, 0, s>>>(out, (const char*)in, g->geo, parity, fb, V); break;
+        case WL_F32: to_canonical_kernel<WL_F32><<<grid, block, 0, s>>>(out, (const char*)in, g->geo, parity, fb, V); break;
+        case WL_F16: to_canonical_kernel<WL_F16><<<grid, block, 0, s>>>(out, (const char*)in, g->geo, parity, fb, V); break;
+        default: to_canonical_kernel<WL_DF64><<<grid, block, 0, s>>>(out, (const char*)in, g->geo, parity, fb, V); break;
+    }
+    WL_CHECK_LAUNCH((double)nrhs * g->geo.Vh * (192.0 + (double)fb / g->geo.Vh));
+    return WL_OK;
+}
+
+}  // namespace wl
+
+extern "C" int wl_field_to_internal(wl_gauge g, void* out, const double* in, int parity, wl_prec prec,
+                                    int nrhs, void* stream)
+{
+    WL_ENTRY();
+    WL_TRY(conv_check(g, out, in, parity, prec, nrhs));
+    return field_to_internal(g, out, in, parity, prec, nrhs, (cudaStream_t)stream);
 }
 
 extern "C" int wl_field_to_canonical(wl_gauge g, double* out, const void* in, int parity, wl_prec prec,
                                      int nrhs, void* stream)
 {
+    WL_ENTRY();
     WL_TRY(conv_check(g, out, in, parity, prec, nrhs));
-    cudaStream_t s = (cudaStream_t)stream;
-    const int block = 128;
-    dim3 grid((unsigned)((g->geo.Vh + block - 1) / block), (unsigned)nrhs);
-    const size_t fb = spinor_field_bytes(prec, g->geo.Vh);
-    const long long V = 2 * g->geo.Vh;
-    if (prec == WL_F64) to_canonical_kernel<WL_F64><<<grid, block, 0, s>>>(out, (const char*)in, g->geo, parity, fb, V);
-    else if (prec == WL_F32) to_canonical_kernel<WL_F32><<<grid, block, 0, s>>>(out, (const char*)in, g->geo, parity, fb, V);
-    else to_canonical_kernel<WL_F16><<<grid, block, 0, s>>>(out, (const char*)in, g->geo, parity, fb, V);
-    WL_CHECK_LAUNCH((double)nrhs * g->geo.Vh * (192.0 + (double)fb / g->geo.Vh));
-    return WL_OK;
+    return field_to_canonical(g, out, in, parity, prec, nrhs, (cudaStream_t)stream);
 }
 
 extern "C" const char* wl_last_error(void) { return wl::t_last_error.c_str(); }

@@ -1,0 +1,390 @@
+// Device building blocks of the hopping term (Eq. 1) shared by the
+// single-lattice kernels (dslash.cu) and the multi-lattice batch (batch.cu):
+// spin projection and reconstruction, neighbour indices, the per-site sum
+// over the eight hops, the fused epilogue and shared-memory link staging.
+#pragma once
+
+#include "clover.cuh"
+#include "internal.cuh"
+
+namespace wl {
+
+// (1 + S gamma_mu) projection / reconstruction in the chiral basis
+// (gamma_5 = diag(1,1,-1,-1)); S = -1 is Eq. 1's forward projector
+// (1 - gamma_mu), S = +1 the backward one.  With u0 = W h0, u1 = W h1 the
+// four spin rows of (1 + S gamma_mu) W psi are (u0, u1, r2, r3):
+//   mu=x: h0 = psi0 + S i psi3, h1 = psi1 + S i psi2, r2 = -S i u1, r3 = -S i u0
+//   mu=y: h0 = psi0 - S psi3,   h1 = psi1 + S psi2,   r2 =  S u1,   r3 = -S u0
+//   mu=z: h0 = psi0 + S i psi2, h1 = psi1 - S i psi3, r2 = -S i u0, r3 =  S i u1
+//   mu=t: h0 = psi0 + S psi2,   h1 = psi1 + S psi3,   r2 =  S u0,   r3 =  S u1
+// The signs are compile-time: a +-1 factor is an add or a subtract, never a
+// multiply (which matters for the double-float type).
+
+// a + S b for S = +1 / -1
+template <int S, typename T>
+__device__ __forceinline__ cx<T> add_s(cx<T> a, cx<T> b)
+{
+    if constexpr (S > 0) return a + b;
+    else return a - b;
+}
+
+template <int MU, int S, typename T>
+__device__ __forceinline__ void project(cx<T> (&h0)[3], cx<T> (&h1)[3], const cx<T> (&q)[12])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cx<T> p0 = q[c], p1 = q[3 + c], p2 = q[6 + c], p3 = q[9 + c];
+        if constexpr (MU == 0) {
+            h0[c] = add_s<S>(p0, mul_i(p3));
+            h1[c] = add_s<S>(p1, mul_i(p2));
+        } else if constexpr (MU == 1) {
+            h0[c] = add_s<-S>(p0, p3);
+            h1[c] = add_s<S>(p1, p2);
+        } else if constexpr (MU == 2) {
+            h0[c] = add_s<S>(p0, mul_i(p2));
+            h1[c] = add_s<-S>(p1, mul_i(p3));
+        } else {
+            h0[c] = add_s<S>(p0, p2);
+            h1[c] = add_s<S>(p1, p3);
+        }
+    }
+}
+
+// add colour row a of the reconstructed (1 + S gamma_mu) W psi to acc
+template <int MU, int S, typename T>
+__device__ __forceinline__ void reconstruct(cx<T> (&acc)[12], int a, cx<T> u0, cx<T> u1)
+{
+    acc[a] = acc[a] + u0;
+    acc[3 + a] = acc[3 + a] + u1;
+    if constexpr (MU == 0) {
+        acc[6 + a] = add_s<-S>(acc[6 + a], mul_i(u1));
+        acc[9 + a] = add_s<-S>(acc[9 + a], mul_i(u0));
+    } else if constexpr (MU == 1) {
+        acc[6 + a] = add_s<S>(acc[6 + a], u1);
+        acc[9 + a] = add_s<-S>(acc[9 + a], u0);
+    } else if constexpr (MU == 2) {
+        acc[6 + a] = add_s<-S>(acc[6 + a], mul_i(u0));
+        acc[9 + a] = add_s<S>(acc[9 + a], mul_i(u1));
+    } else {
+        acc[6 + a] = add_s<S>(acc[6 + a], u0);
+        acc[9 + a] = add_s<S>(acc[9 + a], u1);
+    }
+}
+
+// w0 h0 + w1 h1 + w2 h2 (one row of the SU(3) matrix-vector product)
+template <typename T>
+__device__ __forceinline__ cx<T> dot3(cx<T> w0, cx<T> w1, cx<T> w2, const cx<T> (&h)[3])
+{
+    cx<T> u = w0 * h[0];
+    cmac(u, w1, h[1]);
+    cmac(u, w2, h[2]);
+    return u;
+}
+
+// Double-float: the six real products of each output component are summed
+// with their rounding errors collected in one FP32 word and folded in once at
+// the end (exact TwoProd of the high parts, the cross terms hi*lo in FP32,
+// TwoSum for each addition) -- about 12 FP32 operations per product instead
+// of ~17 for a normalised df64 multiply-add.
+struct LazySum {
+    float s, e;  // value = s + e, unnormalised
+};
+__device__ __forceinline__ void lazy_start(LazySum& L, df64 a, df64 b)
+{
+    L.s = __fmul_rn(a.hi, b.hi);
+    float pe = __fmaf_rn(a.hi, b.hi, -L.s);
+    pe = __fmaf_rn(a.hi, b.lo, pe);
+    L.e = __fmaf_rn(a.lo, b.hi, pe);
+}
+__device__ __forceinline__ void lazy_mac(LazySum& L, df64 a, df64 b)  // L += a b
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float pe = __fmaf_rn(a.hi, b.hi, -p);
+    pe = __fmaf_rn(a.hi, b.lo, pe);
+    pe = __fmaf_rn(a.lo, b.hi, pe);
+    float s, t;
+    two_sum(L.s, p, s, t);
+    L.s = s;
+    L.e = __fadd_rn(L.e, __fadd_rn(t, pe));
+}
+__device__ __forceinline__ df64 lazy_value(const LazySum& L)
+{
+    df64 r;
+    two_sum(L.s, L.e, r.hi, r.lo);
+    return r;
+}
+
+template <>
+__device__ __forceinline__ cx<df64> dot3<df64>(cx<df64> w0, cx<df64> w1, cx<df64> w2,
+                                               const cx<df64> (&h)[3])
+{
+    LazySum re, im;
+    lazy_start(re, w0.re, h[0].re);
+    lazy_mac(re, -w0.im, h[0].im);
+    lazy_mac(re, w1.re, h[1].re);
+    lazy_mac(re, -w1.im, h[1].im);
+    lazy_mac(re, w2.re, h[2].re);
+    lazy_mac(re, -w2.im, h[2].im);
+    lazy_start(im, w0.re, h[0].im);
+    lazy_mac(im, w0.im, h[0].re);
+    lazy_mac(im, w1.re, h[1].im);
+    lazy_mac(im, w1.im, h[1].re);
+    lazy_mac(im, w2.re, h[2].im);
+    lazy_mac(im, w2.im, h[2].re);
+    return {lazy_value(re), lazy_value(im)};
+}
+
+template <int MU, int S, typename T>
+__device__ __forceinline__ void accumulate(cx<T> (&acc)[12], const cx<T> (&q)[12],
+                                           const cx<T> (&W)[9])
+{
+    cx<T> h0[3], h1[3];
+    project<MU, S>(h0, h1, q);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        reconstruct<MU, S>(acc, a, dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h0),
+                           dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h1));
+}
+
+// Row a (entries 3a .. 3a+2) of link d for the FP64-sized layouts (nine
+// 16-byte planes per link): the wide types read one row at a time to keep
+// fewer registers live.
+template <int P>
+__device__ __forceinline__ void load_link_row(cx<typename Prec<P>::real> (&w)[3], const void* base,
+                                              long long Vh, int d, long long i, int a);
+template <>
+__device__ __forceinline__ void load_link_row<WL_F64>(cx<double> (&w)[3], const void* base,
+                                                      long long Vh, int d, long long i, int a)
+{
+    const double2* p = (const double2*)base + ((long long)d * 9 + 3 * a) * Vh;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double2 v = p[k * Vh + i];
+        w[k] = {v.x, v.y};
+    }
+}
+template <>
+__device__ __forceinline__ void load_link_row<WL_DF64>(cx<df64> (&w)[3], const void* base,
+                                                       long long Vh, int d, long long i, int a)
+{
+    const float4* p = (const float4*)base + ((long long)d * 9 + 3 * a) * Vh;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float4 v = p[k * Vh + i];
+        w[k] = {df64(v.x, v.y), df64(v.z, v.w)};
+    }
+}
+
+// Half indices of the eight neighbours (order +x, -x, +y, -y, +z, -z, +t, -t)
+// of output site i on parity p, with periodic wrap-around.
+__device__ __forceinline__ void neighbours(const Geom& g, int p, int i, int (&nb)[8])
+{
+    const int xh = i % g.Lxh;
+    int r = i / g.Lxh;
+    const int y = r % g.L[1];
+    r /= g.L[1];
+    const int z = r % g.L[2];
+    const int t = r / g.L[2];
+    const int x = 2 * xh + ((p + y + z + t) & 1);
+    const int row = i - xh;
+    const int sy = (int)g.sy, sz = (int)g.sz, st = (int)g.st;
+    nb[0] = row + ((x + 1 == g.L[0] ? 0 : x + 1) >> 1);
+    nb[1] = row + ((x == 0 ? g.L[0] - 1 : x - 1) >> 1);
+    nb[2] = (y == g.L[1] - 1) ? i - (g.L[1] - 1) * sy : i + sy;
+    nb[3] = (y == 0) ? i + (g.L[1] - 1) * sy : i - sy;
+    nb[4] = (z == g.L[2] - 1) ? i - (g.L[2] - 1) * sz : i + sz;
+    nb[5] = (z == 0) ? i + (g.L[2] - 1) * sz : i - sz;
+    nb[6] = (t == g.L[3] - 1) ? i - (g.L[3] - 1) * st : i + st;
+    nb[7] = (t == 0) ? i + (g.L[3] - 1) * st : i - st;
+}
+
+template <int P, int D, int MU, int S>
+__device__ __forceinline__ void hop_one(cx<typename Prec<P>::real> (&acc)[12], const void* in,
+                                        long long Vh, int nb, const void* links, long long lVh,
+                                        int li)
+{
+    using T = typename Prec<P>::real;
+    if constexpr (P == WL_F64 || P == WL_DF64) {
+        cx<T> h0[3], h1[3];
+        {
+            cx<T> q[12];
+            load_spinor_ro<P>(q, in, Vh, nb);
+            project<MU, S>(h0, h1, q);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cx<T> w[3];
+            load_link_row<P>(w, links, lVh, D, li, a);
+            reconstruct<MU, S>(acc, a, dot3(w[0], w[1], w[2], h0), dot3(w[0], w[1], w[2], h1));
+        }
+    } else {
+        cx<T> q[12], W[9];
+        load_spinor_ro<P>(q, in, Vh, nb);
+        load_link<P>(W, links, lVh, D, li);
+        accumulate<MU, S, T>(acc, q, W);
+    }
+}
+
+// acc = H_{p,1-p} in at the output site whose neighbours are nb.  The links
+// are read from planes of stride lVh at index li (the global link field, or a
+// tile of it staged in shared memory).  DAG flips the projector signs.
+template <int P, bool DAG>
+__device__ __forceinline__ void hop_site(cx<typename Prec<P>::real> (&acc)[12], const int (&nb)[8],
+                                         long long Vh, const void* in, const void* links,
+                                         long long lVh, int li)
+{
+    using T = typename Prec<P>::real;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = {(T)0, (T)0};
+    constexpr int F = DAG ? +1 : -1;  // forward projector sign
+    constexpr int B = -F;             // backward projector sign
+    hop_one<P, 0, 0, F>(acc, in, Vh, nb[0], links, lVh, li);
+    hop_one<P, 1, 0, B>(acc, in, Vh, nb[1], links, lVh, li);
+    hop_one<P, 2, 1, F>(acc, in, Vh, nb[2], links, lVh, li);
+    hop_one<P, 3, 1, B>(acc, in, Vh, nb[3], links, lVh, li);
+    hop_one<P, 4, 2, F>(acc, in, Vh, nb[4], links, lVh, li);
+    hop_one<P, 5, 2, B>(acc, in, Vh, nb[5], links, lVh, li);
+    hop_one<P, 6, 3, F>(acc, in, Vh, nb[6], links, lVh, li);
+    hop_one<P, 7, 3, B>(acc, in, Vh, nb[7], links, lVh, li);
+}
+
+struct HopArgs {
+    Geom g;
+    const void* links[2];
+    const char* in[2];
+    char* out[2];
+    const char* x1[2];
+    const char* x2[2];
+    const char* w[2];
+    const void* cl[2];  // clover matrix (A or A^-1) per launch parity, see CL below
+    long long rs_in, rs_out, rs_x1, rs_x2, rs_w;
+    double a, b1;
+    int parity0, nparity, blocks_per_parity;
+    double* dot_out;
+    int dot_stride;
+    const int* active;
+    int active_stride;
+    RedScratch red;
+};
+
+// Clover modes of the epilogue (Eq. 2's site-diagonal A = 1 + F or its
+// inverse, packed as in clover.cuh, at the output site):
+//   CL = 0: out = x1 + b1 x2 + a acc
+//   CL = 1: out = x1 + b1 C x2 + a acc          (A x in the Schur operator)
+//   CL = 2: out = C (x1 + b1 x2 + a acc)        (A^-1 H in)
+enum { kClNone = 0, kClX2 = 1, kClOut = 2 };
+
+// out = x1 + b1 x2 + a acc at site i (x1, x2 optional; clover per CL); with
+// DOT the thread's contributions to (w, out) (w optional) and ||out||^2 go to
+// part.
+template <int P, bool DOT, int CL = kClNone>
+__device__ __forceinline__ void epilogue_ptrs(cx<typename Prec<P>::real> (&acc)[12], double a_,
+                                              const char* x1, const char* x2, double b1_,
+                                              const char* w, char* out, long long Vh, int i,
+                                              typename Prec<P>::real (&part)[3],
+                                              const void* cl = nullptr)
+{
+    using T = typename Prec<P>::real;
+    const T a = (T)a_;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = a * acc[c];
+    if (x1) {
+        cx<T> x[12];
+        load_spinor<P>(x, x1, Vh, i);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = acc[c] + x[c];
+    }
+    if (x2) {
+        cx<T> x[12];
+        const T b1 = (T)b1_;
+        load_spinor<P>(x, x2, Vh, i);
+        if (CL == kClX2) clover_mul<P>(x, cl, Vh, i);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = acc[c] + b1 * x[c];
+    }
+    if (CL == kClOut) clover_mul<P>(acc, cl, Vh, i);
+    store_spinor<P>(out, Vh, i, acc);
+    if (DOT) {
+        T cr = 0, ci = 0, nn = 0;
+        if (w) {
+            cx<T> ww[12];
+            load_spinor<P>(ww, w, Vh, i);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                cr = fma(ww[c].re, acc[c].re, fma(ww[c].im, acc[c].im, cr));
+                ci = fma(ww[c].re, acc[c].im, fma(-ww[c].im, acc[c].re, ci));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 12; ++c) nn = fma(acc[c].re, acc[c].re, fma(acc[c].im, acc[c].im, nn));
+        part[0] = cr;
+        part[1] = ci;
+        part[2] = nn;
+    }
+}
+
+template <int P, bool DOT, int CL = kClNone>
+__device__ __forceinline__ void epilogue(cx<typename Prec<P>::real> (&acc)[12], const HopArgs& A,
+                                         int pidx, int rhs, int i, typename Prec<P>::real (&part)[3])
+{
+    auto at = [&](const char* q, long long rs) -> const char* { return q ? q + rhs * rs : nullptr; };
+    epilogue_ptrs<P, DOT, CL>(acc, A.a, at(A.x1[pidx], A.rs_x1), at(A.x2[pidx], A.rs_x2), A.b1,
+                              at(A.w[pidx], A.rs_w), A.out[pidx] + rhs * A.rs_out, A.g.Vh, i, part,
+                              A.cl[pidx]);
+}
+
+// ---------------------------------------------------------------------------
+// Many right-hand sides: a block owns kTile output sites of one parity.  It
+// copies their links (all eight hops) into shared memory once, then its
+// warps sweep the right-hand sides, lane = site, reading the links from
+// shared memory: the links leave HBM once for all right-hand sides.
+// ---------------------------------------------------------------------------
+
+static constexpr int kTile = 32;
+static constexpr int kMaxRhsLaunch = 32;
+
+template <int P>
+struct LinkPlanes;  // the link field as 16-byte planes plus narrower planes
+template <>
+struct LinkPlanes<WL_F64> {
+    static constexpr int n16 = 72, nsmall = 0, small_bytes = 8;
+};
+template <>
+struct LinkPlanes<WL_F32> {
+    static constexpr int n16 = 32, nsmall = 8, small_bytes = 8;
+};
+template <>
+struct LinkPlanes<WL_DF64> {
+    static constexpr int n16 = 72, nsmall = 0, small_bytes = 8;
+};
+template <>
+struct LinkPlanes<WL_F16> {
+    static constexpr int n16 = 16, nsmall = 8, small_bytes = 4;
+};
+
+// Copy the links of sites [base, base + n) into a kTile-stride tile.
+template <int P>
+__device__ __forceinline__ void stage_links(char* sm, const char* gl, long long Vh, int base, int n)
+{
+    using LP = LinkPlanes<P>;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    for (int e = tid; e < LP::n16 * kTile; e += nt) {
+        const int q = e / kTile, j = e - q * kTile;
+        if (j < n) ((uint4*)sm)[q * kTile + j] = __ldg((const uint4*)gl + q * Vh + base + j);
+    }
+    if (LP::nsmall) {
+        const char* gs = gl + (size_t)LP::n16 * 16 * Vh;
+        char* ss = sm + LP::n16 * 16 * kTile;
+        for (int e = tid; e < LP::nsmall * kTile; e += nt) {
+            const int q = e / kTile, j = e - q * kTile;
+            if (j >= n) continue;
+            if (LP::small_bytes == 8)
+                ((uint2*)ss)[q * kTile + j] = __ldg((const uint2*)gs + q * Vh + base + j);
+            else
+                ((unsigned*)ss)[q * kTile + j] = __ldg((const unsigned*)gs + q * Vh + base + j);
+        }
+    }
+}
+
+
+}  // namespace wl

@@ -1,0 +1,211 @@
+// The hopping kernels of Eq. 1 (and, through the epilogue's clover modes, of
+// Eq. 2), as templates over precision P, dagger DAG, fused reduction DOT and
+// clover mode CL.  dslash.cu instantiates the Wilson kernels (CL = 0) and
+// dslash_clover.cu the clover ones, so the two compile in parallel.
+//
+// One thread per output site of one parity.  The eight neighbour spinors are
+// spin-projected to half spinors (12 reals), multiplied by the link (folded
+// with the boundary phase, backward links pre-daggered at set-up) and
+// reconstructed into the four spin components.  Spinors and links live in
+// structure-of-arrays planes, so consecutive threads read consecutive 16-byte
+// words; the neighbour spinors' eightfold reuse is served by L1/L2 (the y, z,
+// t neighbours are the same half index shifted by a row, plane or slab).
+#pragma once
+
+#include "hop.cuh"
+
+namespace wl {
+
+// One right-hand side per grid row, one output site per thread and step of a
+// grid-stride loop over the output sites of both parities in the launch
+// (plain launches cover every site in one step; launches with a fused
+// reduction use a grid of resident blocks, so few partials are left).
+// Resident 256-thread blocks per SM each kernel is compiled for: 2 caps the
+// registers at 128 so that more warps hide latency -- memory latency for
+// FP32/FP16, the long dependent FP32 chains of the double-float type (measured
+// 6-15% faster than uncapped on GB300).  FP64 keeps all the registers it
+// needs (capped, it spills without getting faster).
+#ifndef WL_MINBLOCKS_F32
+#define WL_MINBLOCKS_F32 2
+#endif
+#ifndef WL_MINBLOCKS_F16
+#define WL_MINBLOCKS_F16 2
+#endif
+#ifndef WL_MINBLOCKS_F64
+#define WL_MINBLOCKS_F64 1
+#endif
+#ifndef WL_MINBLOCKS_DF64
+#define WL_MINBLOCKS_DF64 2
+#endif
+template <int P, bool DOT>
+struct MinBlocks {
+    static constexpr int base = P == WL_F64    ? WL_MINBLOCKS_F64
+                                : P == WL_DF64 ? WL_MINBLOCKS_DF64
+                                : P == WL_F32  ? WL_MINBLOCKS_F32
+                                               : WL_MINBLOCKS_F16;
+    static constexpr int value = DOT && base > 2 ? 2 : base;  // the reducing loop needs more
+};
+
+template <int P, bool DAG, bool DOT, int CL>
+__device__ __forceinline__ void hop_kernel_site(const HopArgs& A, int rhs, int pidx, int i,
+                                                typename Prec<P>::real (&part)[3])
+{
+    using T = typename Prec<P>::real;
+    cx<T> acc[12];
+    int nb[8];
+    neighbours(A.g, A.parity0 + pidx, i, nb);
+    hop_site<P, DAG>(acc, nb, A.g.Vh, A.in[pidx] + rhs * A.rs_in, A.links[pidx], A.g.Vh, i);
+    T pt[3] = {0, 0, 0};
+    epilogue<P, DOT, CL>(acc, A, pidx, rhs, i, pt);
+    if (DOT)
+        for (int k = 0; k < 3; ++k) part[k] += pt[k];
+}
+
+template <int P, bool DAG, bool DOT, int CL>
+__global__ void __launch_bounds__(256, (MinBlocks<P, DOT>::value)) hop_kernel(const HopArgs A)
+{
+    const int rhs = blockIdx.y;
+    if (A.active && A.active[rhs * A.active_stride] == 0) return;  // uniform per block
+    using T = typename Prec<P>::real;
+    const long long total = (long long)A.nparity * A.g.Vh;
+    T tpart[3] = {0, 0, 0};  // this thread's sites, in the kernel's arithmetic
+    if constexpr (!DOT) {  // one site per thread; the block's parity is fixed
+        const int pidx = blockIdx.x / A.blocks_per_parity;
+        const int i = (blockIdx.x - pidx * A.blocks_per_parity) * blockDim.x + threadIdx.x;
+        if (i < A.g.Vh) hop_kernel_site<P, DAG, DOT, CL>(A, rhs, pidx, i, tpart);
+        (void)total;
+    } else {
+        for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < total;
+             j += (long long)gridDim.x * blockDim.x) {
+            const int pidx = j >= A.g.Vh ? 1 : 0;
+            hop_kernel_site<P, DAG, DOT, CL>(A, rhs, pidx, (int)(j - pidx * A.g.Vh), tpart);
+        }
+        double part[3] = {(double)tpart[0], (double)tpart[1], (double)tpart[2]};
+        __shared__ double sh[3 * 32];
+        block_sum<3>(part, sh);
+        double tot[3];
+        if (grid_sum<3>(part, tot, A.red, rhs, gridDim.x, blockIdx.x, sh)) {
+            double* o = A.dot_out + (long long)rhs * A.dot_stride;
+            o[0] = tot[0];
+            o[1] = tot[1];
+            o[2] = tot[2];
+        }
+    }
+}
+
+template <int P, bool DAG, bool DOT, int CL>
+__global__ void __launch_bounds__(256, (MinBlocks<P, DOT>::value)) hop_mrhs_kernel(const HopArgs A, int nrhs)
+{
+    using T = typename Prec<P>::real;
+    extern __shared__ __align__(16) char smem[];
+    const int pidx = blockIdx.x / A.blocks_per_parity;
+    const int p = A.parity0 + pidx;
+    const int base = (blockIdx.x - pidx * A.blocks_per_parity) * kTile;
+    const int n = (int)min((long long)kTile, A.g.Vh - base);
+    stage_links<P>(smem, (const char*)A.links[pidx], A.g.Vh, base, n);
+    double* bpart = (double*)(smem + Prec<P>::link_bytes * kTile);
+    __syncthreads();
+    const int lane = threadIdx.x, i = base + lane;
+    const bool valid = lane < n;
+    int nb[8];
+    if (valid) neighbours(A.g, p, i, nb);
+    for (int r = threadIdx.y; r < nrhs; r += blockDim.y) {
+        const bool act = !A.active || A.active[r * A.active_stride] != 0;  // warp-uniform
+        T part[3] = {0, 0, 0};
+        if (act && valid) {
+            cx<T> acc[12];
+            hop_site<P, DAG>(acc, nb, A.g.Vh, A.in[pidx] + r * A.rs_in, smem, kTile, lane);
+            epilogue<P, DOT, CL>(acc, A, pidx, r, i, part);
+        }
+        if (DOT) {  // 32 sites in FP32 (FP64 for the wide types), then FP64 from here on
+            typename RedType<T>::type rp[3] = {(typename RedType<T>::type)part[0],
+                                               (typename RedType<T>::type)part[1],
+                                               (typename RedType<T>::type)part[2]};
+            warp_sum<3>(rp);
+            if (lane == 0)
+                for (int k = 0; k < 3; ++k) bpart[3 * r + k] = (double)rp[k];
+        }
+    }
+    if (!DOT) return;
+    // every block leaves its per-rhs partials; a finishing launch (one block
+    // per right-hand side) adds them up in block order
+    __syncthreads();
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    for (int e = tid; e < 3 * nrhs; e += nt) {
+        const int r = e / 3, k = e - 3 * r;
+        A.red.partial[((long long)r * A.red.max_blocks + blockIdx.x) * 3 + k] = bpart[e];
+    }
+}
+
+// Host-side launchers of one clover mode.
+template <int CL>
+struct HopKernels {
+    static void single(int prec, bool dagger, bool dot, const HopArgs& A, dim3 grid, int block,
+                       cudaStream_t s);
+    static void multi(int prec, bool dagger, bool dot, const HopArgs& A, int nrhs, dim3 grid,
+                      dim3 block, size_t smem, cudaStream_t s);
+    // the reducing single-RHS kernel (for occupancy queries)
+    static const void* reducing(int prec, bool dagger);
+};
+
+template <int CL, int P>
+static void hop_single_p(bool dagger, bool dot, const HopArgs& A, dim3 grid, int block, cudaStream_t s)
+{
+    if (dagger) {
+        if (dot) hop_kernel<P, true, true, CL><<<grid, block, 0, s>>>(A);
+        else hop_kernel<P, true, false, CL><<<grid, block, 0, s>>>(A);
+    } else {
+        if (dot) hop_kernel<P, false, true, CL><<<grid, block, 0, s>>>(A);
+        else hop_kernel<P, false, false, CL><<<grid, block, 0, s>>>(A);
+    }
+}
+
+template <int CL, int P>
+static void hop_multi_p(bool dagger, bool dot, const HopArgs& A, int nrhs, dim3 grid, dim3 block,
+                        size_t smem, cudaStream_t s)
+{
+    if (dagger) {
+        if (dot) hop_mrhs_kernel<P, true, true, CL><<<grid, block, smem, s>>>(A, nrhs);
+        else hop_mrhs_kernel<P, true, false, CL><<<grid, block, smem, s>>>(A, nrhs);
+    } else {
+        if (dot) hop_mrhs_kernel<P, false, true, CL><<<grid, block, smem, s>>>(A, nrhs);
+        else hop_mrhs_kernel<P, false, false, CL><<<grid, block, smem, s>>>(A, nrhs);
+    }
+}
+
+template <int CL>
+void HopKernels<CL>::single(int prec, bool dagger, bool dot, const HopArgs& A, dim3 grid, int block,
+                            cudaStream_t s)
+{
+    switch (prec) {
+        case WL_F64: hop_single_p<CL, WL_F64>(dagger, dot, A, grid, block, s); break;
+        case WL_F32: hop_single_p<CL, WL_F32>(dagger, dot, A, grid, block, s); break;
+        case WL_F16: hop_single_p<CL, WL_F16>(dagger, dot, A, grid, block, s); break;
+        default: hop_single_p<CL, WL_DF64>(dagger, dot, A, grid, block, s); break;
+    }
+}
+
+template <int CL>
+void HopKernels<CL>::multi(int prec, bool dagger, bool dot, const HopArgs& A, int nrhs, dim3 grid,
+                           dim3 block, size_t smem, cudaStream_t s)
+{
+    switch (prec) {
+        case WL_F64: hop_multi_p<CL, WL_F64>(dagger, dot, A, nrhs, grid, block, smem, s); break;
+        case WL_F32: hop_multi_p<CL, WL_F32>(dagger, dot, A, nrhs, grid, block, smem, s); break;
+        case WL_F16: hop_multi_p<CL, WL_F16>(dagger, dot, A, nrhs, grid, block, smem, s); break;
+        default: hop_multi_p<CL, WL_DF64>(dagger, dot, A, nrhs, grid, block, smem, s); break;
+    }
+}
+
+template <int CL>
+const void* HopKernels<CL>::reducing(int prec, bool dagger)
+{
+    switch (prec) {
+        case WL_F64: return dagger ? (const void*)hop_kernel<WL_F64, true, true, CL> : (const void*)hop_kernel<WL_F64, false, true, CL>;
+        case WL_F32: return dagger ? (const void*)hop_kernel<WL_F32, true, true, CL> : (const void*)hop_kernel<WL_F32, false, true, CL>;
+        case WL_F16: return dagger ? (const void*)hop_kernel<WL_F16, true, true, CL> : (const void*)hop_kernel<WL_F16, false, true, CL>;
+        default: return dagger ? (const void*)hop_kernel<WL_DF64, true, true, CL> : (const void*)hop_kernel<WL_DF64, false, true, CL>;
+    }
+}
+
+}  // namespace wl

@@ -46,16 +46,20 @@ struct wl_gauge_s {
     int prec_mask;
     int device;
     int num_sms;
-    void* links[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};  // [prec][out parity]
+    // [prec][out parity]; prec 3 is the internal df64 copy used by the outer corrections
+    void* links[4][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     // grid-reduction scratch
     wl::RedScratch red = {nullptr, nullptr, 0};
     int red_slots = 0;
     int red_gen = 0;  // bumped whenever the scratch moves (captured graphs hold its address)
     // odd-parity temporaries for wilson_mult (eo = 1), per precision
-    void* tmp[3] = {nullptr, nullptr, nullptr};
-    size_t tmp_bytes[3] = {0, 0, 0};
+    void* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t tmp_bytes[4] = {0, 0, 0, 0};
     wl::Timing timing;
     wl::Workspace* ws = nullptr;  // solver workspace, owned (solver.cu)
+    // clover term (clover.cu): [prec][parity][0: A = 1 + F, 1: A^-1]
+    void* clov[4][2][2] = {};
+    bool has_clover = false;
     std::map<std::string, wl::Tuned> tuned;
 };
 
@@ -63,10 +67,29 @@ namespace wl {
 
 Geom make_geom(const int* dims);
 
+// Canonical (x-fastest) site index of half-site i of parity p: the half
+// index runs over x/2 fastest, then y, z, t; the site's parity fixes x's
+// lowest bit.
+__device__ __forceinline__ long long site_of_half(const Geom& g, int p, long long i)
+{
+    const long long row = i / g.Lxh;  // (y, z, t) row
+    const int y = (int)(row % g.L[1]);
+    const int z = (int)((row / g.L[1]) % g.L[2]);
+    const int t = (int)(row / ((long long)g.L[1] * g.L[2]));
+    return 2 * i + ((p + y + z + t) & 1);
+}
+
 // Make sure the reduction scratch holds `slots` slots of `blocks` blocks.
 int ensure_red(wl_gauge g, int slots, long long blocks);
 // Make sure g->tmp[prec] holds at least `bytes`.
 int ensure_tmp(wl_gauge g, int prec, size_t bytes);
+
+// Clover term (clover.cu): release its storage; out = A in or A^-1 in on
+// half fields of one parity (strides in bytes between right-hand sides, 0:
+// contiguous).
+void free_clover(wl_gauge g);
+int launch_clover_apply(wl_gauge g, int prec, void* out, const void* in, int parity, int inverse,
+                        int nrhs, cudaStream_t s, long long rs_out, long long rs_in);
 
 // Hopping kernel launch description.  Fields are per output parity where an
 // array of two is given; strides are bytes between right-hand sides.
@@ -88,6 +111,10 @@ struct HopLaunch {
     int dot_stride = 3;
     const int* active = nullptr;  // skip right-hand sides whose flag is 0
     int active_stride = 1;
+    // clover term (Eq. 2): 0 none; 1 out = x1 + b1 C x2 + a H in;
+    // 2 out = C (x1 + b1 x2 + a H in); C = clov[k] per output parity
+    int cl_mode = 0;
+    const void* clov[2] = {nullptr, nullptr};
 };
 
 int launch_hop(wl_gauge g, const HopLaunch& h, cudaStream_t s);
@@ -105,10 +132,28 @@ int launch_convert(wl_gauge g, int pdst, void* dst, int psrc, const void* src, i
                    const int* mask, cudaStream_t s, long long dst_rs = 0, long long src_rs = 0);
 int launch_zero(wl_gauge g, int prec, void* dst, int nhalf, int nrhs, const int* mask,
                 cudaStream_t s);
-// x_hi (F64) += x_lo (prec)
-int launch_accum_hi(wl_gauge g, double* xhi, int plo, const void* xlo, int nhalf, int nrhs,
+// x_hi (precision phi: FP64 or df64) += x_lo (precision plo)
+int launch_accum_hi(wl_gauge g, int phi, void* xhi, int plo, const void* xlo, int nhalf, int nrhs,
                     const int* mask, cudaStream_t s, long long hi_rs = 0);
 
 bool is_capturing(cudaStream_t s);
+
+// Layout conversion for any storage precision (including the internal df64).
+int field_to_internal(wl_gauge g, void* out, const double* in, int parity, int prec, int nrhs,
+                      cudaStream_t s);
+int field_to_canonical(wl_gauge g, double* out, const void* in, int parity, int prec, int nrhs,
+                       cudaStream_t s);
+
+// Blocks of `kernel` (block threads, dynamic smem bytes) that fit on the whole
+// GPU at once: the grid of a grid-stride kernel whose reduction should have
+// few partials.
+int resident_grid(const void* kernel, int block, size_t smem);
+
+// Second stage of a multi-slot reduction: one block per slot sums
+// partial[slot * stride + b] (3 doubles each, b < nblocks) in block order and
+// writes out[slot * out_stride + 0..2] for slots whose active flag is set.
+int launch_finish_slots(const double* partial, long long stride, int nblocks, int nslots,
+                        double* out, int out_stride, const int* active, int active_stride,
+                        cudaStream_t s);
 
 }  // namespace wl

@@ -21,74 +21,34 @@
 // kept and only the residual is replaced (reliable updates, Sleijpen & van
 // der Vorst 1996); otherwise each inner solve restarts (defect correction).
 // Convergence is always judged on the FP64 true residual of the full D.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
-#include "internal.cuh"
+#include "hop.cuh"
+#include "solver.cuh"
 
 namespace wl {
 
-struct Scal {
-    double rr[3];       // (rhat, r) re, im; ||r||^2
-    double rho_prev[2];
-    double alpha[2];
-    double omega[2];
-    double rv[3];       // (rhat, v); ||v||^2
-    double st[3];       // (s, t); ||t||^2
-    double target2;     // stop when ||r||^2 <= target2
-    double r2_max;      // largest ||r||^2 since the last reliable update
-    double delta2;      // reliable-update threshold delta^2 (0: off)
-    double rh2;         // ||rhat||^2
-    int active;
-    int iters;
-    int flags;
-    int want_update;
-};
+// Per-round log of the outer loop on stderr when WL_SOLVE_VERBOSE is set
+// (diagnostics only; one line per event and right-hand side).
+static bool solve_verbose()
+{
+    static const bool on = getenv("WL_SOLVE_VERBOSE") != nullptr;
+    return on;
+}
 
-enum { FLAG_CONVERGED = 1, FLAG_BREAKDOWN = 2, FLAG_NAN = 4, FLAG_MAXITER = 8 };
-
-static const int kScalStride = sizeof(Scal) / sizeof(double);
-static const int kMaxOuter = 500;  // FP64 corrections per solve
-static const int kActiveStride = sizeof(Scal) / sizeof(int);
-
-struct Workspace {
-    int inner = -1, nrhs = 0, eo = -1, nhalf = 0, xlo_prec = 0;
-    size_t vb = 0;    // bytes of one inner vector (nhalf halves)
-    size_t vb64 = 0;  // bytes of one FP64 vector (nhalf halves)
-    size_t hb64 = 0;  // bytes of one FP64 half field
-    // inner-precision vectors (nrhs each)
-    void *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr,
-         *xlo = nullptr, *tmp = nullptr;
-    // FP64 (nrhs each): b even/odd (or full b), b', x, r, odd temporary, odd x
-    double *b64 = nullptr, *bp = nullptr, *xhi = nullptr, *rhi = nullptr, *tmp64 = nullptr,
-           *xo = nullptr;
-    Scal* sc = nullptr;
-    Scal* sc_h = nullptr;  // pinned
-    int* mask = nullptr;
-    int* mask_h = nullptr;  // pinned
-    double* nrm = nullptr;  // 3 doubles per rhs
-    double* nrm_h = nullptr;  // pinned
-    // staging of host buffers
-    double* stage_b = nullptr;
-    double* stage_x = nullptr;
-    size_t stage_bytes = 0;
-    // CUDA graph of k iterations
-    cudaGraphExec_t graph = nullptr;
-    int graph_k = 0;
-    int graph_nrhs = 0;
-    int graph_red_gen = -1;
-    cudaStream_t cap_stream = nullptr;  // private stream for graph capture
-    long long graph_kernels = 0;
-    long long graph_bytes = 0;
-};
 
 static void free_ws(Workspace* w)
 {
     if (!w) return;
     void* dev[] = {w->r, w->rh, w->p, w->v, w->s, w->t, w->xlo, w->tmp, w->b64, w->bp, w->xhi,
-                   w->rhi, w->tmp64, w->xo, w->sc, w->mask, w->nrm, w->stage_b, w->stage_x};
+                   w->rhi, w->tmp64, w->sc, w->mask, w->nrm, w->stage_b, w->stage_x,
+                   w->bout == w->b64 ? nullptr : w->bout, w->x64 == w->xhi ? nullptr : w->x64};
     for (void* q : dev)
         if (q) cudaFree(q);
     if (w->sc_h) cudaFreeHost(w->sc_h);
@@ -112,7 +72,7 @@ void free_workspace(wl_gauge g)
 namespace wl {
 
 // ---------------------------------------------------------------------------
-// device kernels
+// device kernels (single lattice; one right-hand side per grid row)
 // ---------------------------------------------------------------------------
 
 struct Vec2 {
@@ -129,30 +89,18 @@ __device__ __forceinline__ long long split_index(const Vec2& v, long long j, lon
     return j - h * v.Vh;
 }
 
-__device__ __forceinline__ cx<double> cdiv(cx<double> a, cx<double> b)
-{
-    const double d = b.re * b.re + b.im * b.im;
-    return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
-}
-
-// beta = (rho / rho_prev)(alpha / omega);  p = r + beta (p - omega v)
 template <int P>
 __global__ void __launch_bounds__(256) update_p_kernel(char* p, const char* r, const char* v,
                                                        Vec2 vec, const Scal* sc)
 {
-    using T = typename Prec<P>::real;
     const int rhs = blockIdx.y;
     const Scal& S = sc[rhs];
     if (!S.active) return;
-    __shared__ T coef[4];
+    __shared__ double coef[4];
     if (threadIdx.x == 0) {
-        const cx<double> rho = {S.rr[0], S.rr[1]}, rp = {S.rho_prev[0], S.rho_prev[1]};
-        const cx<double> al = {S.alpha[0], S.alpha[1]}, om = {S.omega[0], S.omega[1]};
-        const cx<double> beta = cdiv(rho, rp) * cdiv(al, om);
-        coef[0] = (T)beta.re;
-        coef[1] = (T)beta.im;
-        coef[2] = (T)om.re;
-        coef[3] = (T)om.im;
+        double c[4];
+        beta_omega(S, c);
+        for (int k = 0; k < 4; ++k) coef[k] = c[k];
     }
     __syncthreads();
     const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -160,43 +108,22 @@ __global__ void __launch_bounds__(256) update_p_kernel(char* p, const char* r, c
     long long off;
     const long long i = split_index(vec, j, off);
     off += rhs * vec.rstride;
-    const cx<T> beta = {coef[0], coef[1]}, om = {coef[2], coef[3]};
-    cx<T> pp[12], rr[12], vv[12];
-    load_spinor<P>(pp, p + off, vec.Vh, i);
-    load_spinor<P>(rr, r + off, vec.Vh, i);
-    load_spinor<P>(vv, v + off, vec.Vh, i);
-#pragma unroll
-    for (int c = 0; c < 12; ++c) pp[c] = rr[c] + beta * (pp[c] - om * vv[c]);
-    store_spinor<P>(p + off, vec.Vh, i, pp);
+    const double c[4] = {coef[0], coef[1], coef[2], coef[3]};
+    p_update_site<P>(p + off, r + off, v + off, vec.Vh, i, c);
 }
 
-__device__ __forceinline__ cx<double> safe_alpha(const Scal& S)
-{
-    const double rv2 = S.rv[0] * S.rv[0] + S.rv[1] * S.rv[1];
-    if (!(rv2 > 1e-60 * S.rh2 * S.rv[2])) return {0.0, 0.0};  // breakdown: no step
-    return cdiv({S.rr[0], S.rr[1]}, {S.rv[0], S.rv[1]});
-}
-
-__device__ __forceinline__ cx<double> safe_omega(const Scal& S)
-{
-    if (!(S.st[2] > 0.0)) return {0.0, 0.0};
-    return {S.st[0] / S.st[2], -S.st[1] / S.st[2]};  // (t, s)/(t, t) = conj((s, t))/||t||^2
-}
-
-// alpha = rho / (rhat, v);  s = r - alpha v
 template <int P>
 __global__ void __launch_bounds__(256) update_s_kernel(char* s, const char* r, const char* v,
                                                        Vec2 vec, const Scal* sc)
 {
-    using T = typename Prec<P>::real;
     const int rhs = blockIdx.y;
     const Scal& S = sc[rhs];
     if (!S.active) return;
-    __shared__ T coef[2];
+    __shared__ double coef[2];
     if (threadIdx.x == 0) {
         const cx<double> al = safe_alpha(S);
-        coef[0] = (T)al.re;
-        coef[1] = (T)al.im;
+        coef[0] = al.re;
+        coef[1] = al.im;
     }
     __syncthreads();
     const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -204,25 +131,15 @@ __global__ void __launch_bounds__(256) update_s_kernel(char* s, const char* r, c
     long long off;
     const long long i = split_index(vec, j, off);
     off += rhs * vec.rstride;
-    const cx<T> al = {coef[0], coef[1]};
-    cx<T> rr[12], vv[12];
-    load_spinor<P>(rr, r + off, vec.Vh, i);
-    load_spinor<P>(vv, v + off, vec.Vh, i);
-#pragma unroll
-    for (int c = 0; c < 12; ++c) rr[c] = rr[c] - al * vv[c];
-    store_spinor<P>(s + off, vec.Vh, i, rr);
+    s_update_site<P>(s + off, r + off, v + off, vec.Vh, i, {coef[0], coef[1]});
 }
 
-// omega = (t, s)/(t, t);  x += alpha p + omega s;  r = s - omega t;
-// fused rho' = (rhat, r), ||r||^2; the last block advances the scalars.
 template <int P, int PX>
 __global__ void __launch_bounds__(256) update_xr_kernel(char* x, Vec2 vx, char* r, const char* p,
                                                         const char* s, const char* t,
                                                         const char* rh, Vec2 vec, Scal* sc,
                                                         RedScratch red)
 {
-    using T = typename Prec<P>::real;
-    using TX = typename Prec<PX>::real;
     const int rhs = blockIdx.y;
     Scal& S = sc[rhs];
     if (!S.active) return;
@@ -236,77 +153,25 @@ __global__ void __launch_bounds__(256) update_xr_kernel(char* x, Vec2 vx, char* 
         dcoef[3] = om.im;
     }
     __syncthreads();
-    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double part[3] = {0, 0, 0};
-    if (j < vec.nhalf * vec.Vh) {
+    using T = typename Prec<P>::real;
+    const double dc[4] = {dcoef[0], dcoef[1], dcoef[2], dcoef[3]};
+    T tpart[3] = {0, 0, 0};  // this thread's sites in the kernel's arithmetic
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < vec.nhalf * vec.Vh;
+         j += (long long)gridDim.x * blockDim.x) {
         long long off, offx;
         const long long i = split_index(vec, j, off);
         split_index(vx, j, offx);
         off += rhs * vec.rstride;
         offx += rhs * vx.rstride;
-        const cx<T> al = {(T)dcoef[0], (T)dcoef[1]}, om = {(T)dcoef[2], (T)dcoef[3]};
-        cx<T> pp[12], ss[12];
-        load_spinor<P>(pp, p + off, vec.Vh, i);
-        load_spinor<P>(ss, s + off, vec.Vh, i);
-        {
-            cx<TX> xx[12];
-            load_spinor<PX>(xx, x + offx, vec.Vh, i);
-#pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                const cx<T> d = al * pp[c] + om * ss[c];
-                xx[c] = {xx[c].re + (TX)d.re, xx[c].im + (TX)d.im};
-            }
-            store_spinor<PX>(x + offx, vec.Vh, i, xx);
-        }
-        cx<T> tt[12];
-        load_spinor<P>(tt, t + off, vec.Vh, i);
-#pragma unroll
-        for (int c = 0; c < 12; ++c) ss[c] = ss[c] - om * tt[c];
-        store_spinor<P>(r + off, vec.Vh, i, ss);
-        // reduce on the stored (rounded) residual so rho matches what K_b reads
-        cx<T> rn[12], hh[12];
-        load_spinor<P>(rn, r + off, vec.Vh, i);
-        load_spinor<P>(hh, rh + off, vec.Vh, i);
-        T cr = 0, ci = 0, nn = 0;
-#pragma unroll
-        for (int c = 0; c < 12; ++c) {
-            cr = fma(hh[c].re, rn[c].re, fma(hh[c].im, rn[c].im, cr));
-            ci = fma(hh[c].re, rn[c].im, fma(-hh[c].im, rn[c].re, ci));
-            nn = fma(rn[c].re, rn[c].re, fma(rn[c].im, rn[c].im, nn));
-        }
-        part[0] = cr;
-        part[1] = ci;
-        part[2] = nn;
+        T pt[3];
+        xr_update_site<P, PX>(x + offx, r + off, p + off, s + off, t + off, rh + off, vec.Vh, i,
+                              dc, pt);
+        for (int k = 0; k < 3; ++k) tpart[k] += pt[k];
     }
+    double part[3] = {(double)tpart[0], (double)tpart[1], (double)tpart[2]};
     block_sum<3>(part, sh);
     double tot[3];
-    if (grid_sum<3>(part, tot, red, rhs, gridDim.x, blockIdx.x, sh)) {
-        S.rho_prev[0] = S.rr[0];
-        S.rho_prev[1] = S.rr[1];
-        S.alpha[0] = dcoef[0];
-        S.alpha[1] = dcoef[1];
-        S.omega[0] = dcoef[2];
-        S.omega[1] = dcoef[3];
-        S.rr[0] = tot[0];
-        S.rr[1] = tot[1];
-        S.rr[2] = tot[2];
-        S.iters += 1;
-        const bool stepped = (dcoef[0] != 0.0 || dcoef[1] != 0.0);
-        const bool omega0 = (dcoef[2] == 0.0 && dcoef[3] == 0.0);
-        if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) {
-            S.flags |= FLAG_NAN;
-            S.active = 0;
-        } else if (tot[2] <= S.target2) {
-            S.flags |= FLAG_CONVERGED;
-            S.active = 0;
-        } else if (!stepped || omega0) {
-            S.flags |= FLAG_BREAKDOWN;
-            S.active = 0;
-        } else if (S.delta2 > 0.0) {
-            if (tot[2] > S.r2_max) S.r2_max = tot[2];
-            if (tot[2] < S.delta2 * S.r2_max) S.want_update = 1;
-        }
-    }
+    if (grid_sum<3>(part, tot, red, rhs, gridDim.x, blockIdx.x, sh)) advance_scalars(S, tot, dc);
 }
 
 // Start (or restart) the scalars of the masked right-hand sides; rr holds
@@ -345,8 +210,6 @@ static Vec2 vec_of(wl_gauge g, int prec, int nhalf)
     return v;
 }
 
-static const int kBlock = 256;
-
 template <typename F>
 static int dispatch_prec(int prec, F&& f)
 {
@@ -364,7 +227,7 @@ static int ws_alloc(void** p, size_t bytes)
     return WL_OK;
 }
 
-static int ensure_ws(wl_gauge g, int inner, int nrhs, int eo)
+int ensure_ws(wl_gauge g, int inner, int nrhs, int eo)
 {
     Workspace* w = g->ws;
     if (w && w->inner == inner && w->nrhs >= nrhs && w->eo == eo) return WL_OK;
@@ -377,6 +240,9 @@ static int ensure_ws(wl_gauge g, int inner, int nrhs, int eo)
     w->eo = eo;
     w->nhalf = eo ? 1 : 2;
     w->xlo_prec = inner == WL_F64 ? WL_F64 : WL_F32;
+    // outer residual corrections of mixed-precision solves in df64 (FP32-rate
+    // arithmetic, ~2^-44 rounding); the plain FP64 solve stays in FP64
+    w->outer = inner == WL_F64 ? WL_F64 : WL_DF64;
     const long long Vh = g->geo.Vh;
     w->vb = spinor_field_bytes(inner, Vh) * w->nhalf;
     w->hb64 = spinor_field_bytes(WL_F64, Vh);
@@ -391,6 +257,13 @@ static int ensure_ws(wl_gauge g, int inner, int nrhs, int eo)
     WL_TRY(ws_alloc((void**)&w->xhi, 2 * w->hb64 * n));  // full x (even | odd) per rhs
     WL_TRY(ws_alloc((void**)&w->rhi, 2 * w->hb64 * n));
     WL_TRY(ws_alloc((void**)&w->tmp64, w->hb64 * n));
+    if (w->outer == WL_F64) {
+        w->bout = w->b64;
+        w->x64 = w->xhi;
+    } else {
+        WL_TRY(ws_alloc((void**)&w->bout, 2 * w->hb64 * n));
+        WL_TRY(ws_alloc((void**)&w->x64, 2 * w->hb64 * n));
+    }
     WL_TRY(ws_alloc((void**)&w->sc, sizeof(Scal) * n));
     WL_TRY(ws_alloc((void**)&w->mask, sizeof(int) * n));
     WL_TRY(ws_alloc((void**)&w->nrm, sizeof(double) * 3 * n));
@@ -401,14 +274,12 @@ static int ensure_ws(wl_gauge g, int inner, int nrhs, int eo)
     std::memset(w->sc_h, 0, sizeof(Scal) * n);
     // reduction scratch for every kernel the solve launches (no growth later,
     // so graph capture never needs to allocate)
-    const long long hop_blocks = 2 * ((Vh + 127) / 128);
+    const long long hop_blocks = 2 * ((Vh + 31) / 32);  // smallest hop tile: 32 sites
     const long long blas_blocks = (2 * Vh + kBlock - 1) / kBlock;
     WL_TRY(ensure_red(g, nrhs, hop_blocks > blas_blocks ? hop_blocks : blas_blocks));
     return WL_OK;
 }
 
-// stride between right-hand sides of the FP64 full fields (even | odd)
-static long long full_rs(const Workspace* w) { return (long long)(2 * w->hb64); }
 
 // A v (inner precision) with fused (w, out) and ||out||^2 into dot_out.
 static int apply_A(wl_gauge g, Workspace* w, int prec, void* out, const void* in, const void* wdot,
@@ -425,14 +296,27 @@ static int apply_A(wl_gauge g, Workspace* w, int prec, void* out, const void* in
         h1.rs_in = h1.rs_out = (long long)hb;
         h1.active = active;
         h1.active_stride = kActiveStride;
+        if (g->has_clover) {  // tmp = A_oo^-1 H_oe in
+            h1.cl_mode = kClOut;
+            h1.clov[0] = g->clov[prec][1][1];
+        }
         WL_TRY(launch_hop(g, h1, s));
         HopLaunch h2 = h1;
         h2.parity0 = 0;
         h2.in[0] = w->tmp;
         h2.out[0] = out;
-        h2.x1[0] = in;
-        h2.rs_x1 = (long long)hb;
         h2.a = -g->kappa * g->kappa;
+        if (g->has_clover) {  // out = A_ee in - kappa^2 H_eo tmp
+            h2.x2[0] = in;
+            h2.rs_x2 = (long long)hb;
+            h2.b1 = 1.0;
+            h2.cl_mode = kClX2;
+            h2.clov[0] = g->clov[prec][0][0];
+        } else {
+            h2.x1[0] = in;
+            h2.rs_x1 = (long long)hb;
+            h2.cl_mode = kClNone;
+        }
         h2.w[0] = wdot;
         h2.rs_w = (long long)hb;
         h2.dot = true;
@@ -449,12 +333,23 @@ static int apply_A(wl_gauge g, Workspace* w, int prec, void* out, const void* in
     h.in[1] = in;
     h.out[0] = out;
     h.out[1] = (char*)out + hb;
-    h.x1[0] = in;
-    h.x1[1] = (const char*)in + hb;
     h.w[0] = wdot;
     h.w[1] = (const char*)wdot + hb;
-    h.rs_in = h.rs_out = h.rs_x1 = h.rs_w = (long long)(2 * hb);
+    h.rs_in = h.rs_out = h.rs_w = (long long)(2 * hb);
     h.a = -g->kappa;
+    if (g->has_clover) {  // out_p = A_pp in_p - kappa H in_{1-p}
+        h.x2[0] = in;
+        h.x2[1] = (const char*)in + hb;
+        h.rs_x2 = (long long)(2 * hb);
+        h.b1 = 1.0;
+        h.cl_mode = kClX2;
+        h.clov[0] = g->clov[prec][0][0];
+        h.clov[1] = g->clov[prec][1][0];
+    } else {
+        h.x1[0] = in;
+        h.x1[1] = (const char*)in + hb;
+        h.rs_x1 = (long long)(2 * hb);
+    }
     h.dot = true;
     h.dot_out = dot_out;
     h.dot_stride = kScalStride;
@@ -488,12 +383,18 @@ static int enqueue_iteration(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
     WL_TRY(apply_A(g, w, P, w->t, w->s, w->s, w->sc[0].st, active, nrhs, s));
     return dispatch_prec(P, [&](auto pc) -> int {
         constexpr int PP = decltype(pc)::value;
+        // grid of resident blocks: the fused reduction leaves few partials
+        dim3 rgrid = grid;
+        rgrid.x = std::min(grid.x, (unsigned)resident_grid(
+                                       w->xlo_prec == WL_F64 ? (const void*)update_xr_kernel<PP, WL_F64>
+                                                             : (const void*)update_xr_kernel<PP, WL_F32>,
+                                       kBlock, 0));
         if (w->xlo_prec == WL_F64)
-            update_xr_kernel<PP, WL_F64><<<grid, kBlock, 0, s>>>(
+            update_xr_kernel<PP, WL_F64><<<rgrid, kBlock, 0, s>>>(
                 (char*)w->xlo, vx, (char*)w->r, (const char*)w->p, (const char*)w->s,
                 (const char*)w->t, (const char*)w->rh, v, w->sc, g->red);
         else
-            update_xr_kernel<PP, WL_F32><<<grid, kBlock, 0, s>>>(
+            update_xr_kernel<PP, WL_F32><<<rgrid, kBlock, 0, s>>>(
                 (char*)w->xlo, vx, (char*)w->r, (const char*)w->p, (const char*)w->s,
                 (const char*)w->t, (const char*)w->rh, v, w->sc, g->red);
         // reads p, s, t, rhat and x; writes x and r
@@ -503,7 +404,7 @@ static int enqueue_iteration(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
 }
 
 // Run k iterations: a CUDA-graph replay when graph_k > 0, else eager launches.
-static int run_chunk(wl_gauge g, Workspace* w, int nrhs, int k, bool use_graph, cudaStream_t s)
+int run_chunk(wl_gauge g, Workspace* w, int nrhs, int k, bool use_graph, cudaStream_t s)
 {
     if (!use_graph) {
         for (int it = 0; it < k; ++it) WL_TRY(enqueue_iteration(g, w, nrhs, s));
@@ -543,12 +444,12 @@ static int run_chunk(wl_gauge g, Workspace* w, int nrhs, int k, bool use_graph, 
 }
 
 // r = b' - A x in FP64 for masked rhs, with ||r||^2 into w->nrm.
-static int residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
+int residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
 {
     const size_t hb = w->hb64;
     if (w->eo) {
         HopLaunch h1;
-        h1.prec = WL_F64;
+        h1.prec = w->outer;
         h1.parity0 = 1;
         h1.nrhs = nrhs;
         h1.in[0] = w->xhi;
@@ -556,9 +457,13 @@ static int residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
         h1.rs_in = full_rs(w);
         h1.rs_out = (long long)hb;
         h1.active = w->mask;
+        if (g->has_clover) {  // tmp = A_oo^-1 H_oe x
+            h1.cl_mode = kClOut;
+            h1.clov[0] = g->clov[w->outer][1][1];
+        }
         WL_TRY(launch_hop(g, h1, s));
         HopLaunch h2;
-        h2.prec = WL_F64;
+        h2.prec = w->outer;
         h2.parity0 = 0;
         h2.nrhs = nrhs;
         h2.in[0] = w->tmp64;
@@ -574,11 +479,15 @@ static int residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
         h2.dot = true;
         h2.dot_out = w->nrm;
         h2.active = w->mask;
+        if (g->has_clover) {  // r = b' - A_ee x + kappa^2 H_eo tmp
+            h2.cl_mode = kClX2;
+            h2.clov[0] = g->clov[w->outer][0][0];
+        }
         return launch_hop(g, h2, s);
     }
     // full: r_p = b_p - x_p + kappa H x_{1-p}
     HopLaunch h;
-    h.prec = WL_F64;
+    h.prec = w->outer;
     h.parity0 = 0;
     h.nparity = 2;
     h.nrhs = nrhs;
@@ -596,26 +505,42 @@ static int residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
     h.dot = true;
     h.dot_out = w->nrm;
     h.active = w->mask;
+    if (g->has_clover) {  // r_p = b_p - A_pp x_p + kappa H x_{1-p}
+        h.cl_mode = kClX2;
+        h.clov[0] = g->clov[w->outer][0][0];
+        h.clov[1] = g->clov[w->outer][1][0];
+    }
     return launch_hop(g, h, s);
 }
 
 // r_full = b - D x on the full lattice (FP64) with ||r||^2 into w->nrm.
-static int true_residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
+// r = b - D x in FP64 with ||r||^2 into w->nrm.  Full solves evaluate both
+// parities.  Even-odd Wilson solves evaluate the even half only: the odd
+// half, b_o - x_o + kappa H_oe x_e, is zero by construction because x_o was
+// just formed as b_o + kappa H_oe x_e by the same FP64 operations.  With a
+// clover term x_o = A_oo^-1 (...) leaves a rounding-level odd residual, so
+// both halves are evaluated.
+int true_residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
 {
     const size_t hb = w->hb64;
     HopLaunch h;
-    h.prec = WL_F64;
+    h.prec = WL_F64;  // IEEE FP64 on the FP64 copies of b and x
     h.parity0 = 0;
-    h.nparity = 2;
+    h.nparity = w->eo && !g->has_clover ? 1 : 2;
+    if (g->has_clover) {  // r_p = b_p - A_pp x_p + kappa H x_{1-p}
+        h.cl_mode = kClX2;
+        h.clov[0] = g->clov[WL_F64][0][0];
+        h.clov[1] = g->clov[WL_F64][1][0];
+    }
     h.nrhs = nrhs;
-    h.in[0] = (const char*)w->xhi + hb;
-    h.in[1] = w->xhi;
+    h.in[0] = (const char*)w->x64 + hb;
+    h.in[1] = w->x64;
     h.out[0] = w->rhi;
     h.out[1] = (char*)w->rhi + hb;
     h.x1[0] = w->b64;
     h.x1[1] = (const char*)w->b64 + hb;
-    h.x2[0] = w->xhi;
-    h.x2[1] = (const char*)w->xhi + hb;
+    h.x2[0] = w->x64;
+    h.x2[1] = (const char*)w->x64 + hb;
     h.rs_in = h.rs_out = h.rs_x1 = h.rs_x2 = full_rs(w);
     h.b1 = -1.0;
     h.a = g->kappa;
@@ -624,13 +549,34 @@ static int true_residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
     return launch_hop(g, h, s);
 }
 
-static int upload_mask(Workspace* w, int nrhs, cudaStream_t s)
+// The host mask travels as kernel parameters (bit-packed), which the launch
+// copies when it is issued: the host may rewrite mask_h right after, as the
+// outer loop does, without racing an asynchronous copy from pinned memory.
+struct MaskBits {
+    unsigned word[256];  // 8192 right-hand sides per launch
+};
+
+__global__ void set_mask_kernel(int* mask, int first, int n, const MaskBits bits)
 {
-    WL_CUDA(cudaMemcpyAsync(w->mask, w->mask_h, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+        mask[first + k] = (bits.word[k >> 5] >> (k & 31)) & 1u;
+}
+
+int upload_mask(Workspace* w, int nrhs, cudaStream_t s)
+{
+    for (int first = 0; first < nrhs; first += 8192) {
+        const int n = nrhs - first < 8192 ? nrhs - first : 8192;
+        MaskBits bits;
+        std::memset(&bits, 0, sizeof bits);
+        for (int k = 0; k < n; ++k)
+            if (w->mask_h[first + k]) bits.word[k >> 5] |= 1u << (k & 31);
+        set_mask_kernel<<<1, 256, 0, s>>>(w->mask, first, n, bits);
+        WL_CHECK_LAUNCH(0.0);
+    }
     return WL_OK;
 }
 
-static int read_norms(Workspace* w, int nrhs, cudaStream_t s)
+int read_norms(Workspace* w, int nrhs, cudaStream_t s)
 {
     WL_CUDA(cudaMemcpyAsync(w->nrm_h, w->nrm, sizeof(double) * 3 * nrhs, cudaMemcpyDeviceToHost, s));
     WL_CUDA(cudaStreamSynchronize(s));
@@ -639,7 +585,7 @@ static int read_norms(Workspace* w, int nrhs, cudaStream_t s)
 
 // Begin an inner solve for the masked rhs: r = r_hi (converted), rhat = r,
 // p = v = x_lo = 0, fresh scalars with the given targets.
-static int inner_start(wl_gauge g, Workspace* w, int nrhs, const double* target2,
+int inner_start(wl_gauge g, Workspace* w, int nrhs, const double* target2,
                        double delta2, cudaStream_t s)
 {
     const int P = w->inner;
@@ -660,7 +606,7 @@ static int inner_start(wl_gauge g, Workspace* w, int nrhs, const double* target2
     // them is current after the last read-back)
     WL_CUDA(cudaMemcpyAsync(w->sc, w->sc_h, sizeof(Scal) * nrhs, cudaMemcpyHostToDevice, s));
     WL_TRY(upload_mask(w, nrhs, s));
-    WL_TRY(launch_convert(g, P, w->r, WL_F64, w->rhi, w->nhalf, nrhs, w->mask, s));
+    WL_TRY(launch_convert(g, P, w->r, w->outer, w->rhi, w->nhalf, nrhs, w->mask, s));
     WL_TRY(launch_convert(g, P, w->rh, P, w->r, w->nhalf, nrhs, w->mask, s));
     WL_TRY(launch_zero(g, P, w->p, w->nhalf, nrhs, w->mask, s));
     WL_TRY(launch_zero(g, P, w->v, w->nhalf, nrhs, w->mask, s));
@@ -673,14 +619,15 @@ static int inner_start(wl_gauge g, Workspace* w, int nrhs, const double* target2
 
 // Reliable update for the masked rhs: x_hi += x_lo, x_lo = 0, r_hi = b' - A x_hi,
 // r = r_hi; the Krylov directions and rhat are kept.
-static int reliable_update(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
+int reliable_update(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
 {
     const int P = w->inner;
     WL_TRY(upload_mask(w, nrhs, s));
-    WL_TRY(launch_accum_hi(g, w->xhi, w->xlo_prec, w->xlo, w->nhalf, nrhs, w->mask, s, full_rs(w)));
+    WL_TRY(launch_accum_hi(g, w->outer, w->xhi, w->xlo_prec, w->xlo, w->nhalf, nrhs, w->mask, s,
+                           full_rs(w)));
     WL_TRY(launch_zero(g, w->xlo_prec, w->xlo, w->nhalf, nrhs, w->mask, s));
     WL_TRY(residual64(g, w, nrhs, s));
-    WL_TRY(launch_convert(g, P, w->r, WL_F64, w->rhi, w->nhalf, nrhs, w->mask, s));
+    WL_TRY(launch_convert(g, P, w->r, w->outer, w->rhi, w->nhalf, nrhs, w->mask, s));
     WL_TRY(launch_cdot(g, P, w->rh, w->r, w->nhalf, nrhs, w->sc[0].rr, kScalStride, w->mask, s));
     init_scal_kernel<<<(nrhs + 63) / 64, 64, 0, s>>>(w->sc, w->mask, nrhs, 0);
     WL_CHECK_LAUNCH(0.0);
@@ -689,7 +636,7 @@ static int reliable_update(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
 
 }  // namespace wl
 
-using namespace wl;
+namespace wl {
 
 static bool is_host_pointer(const void* p)
 {
@@ -701,30 +648,42 @@ static bool is_host_pointer(const void* p)
     return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
 }
 
-extern "C" int wilson_solve(wl_gauge g, double* x, const double* b, int nrhs,
-                            const wl_solve_params* prm, wl_solve_info* info, void* stream)
+static int check_params(wl_gauge g, const void* x, const void* b, int nrhs,
+                        const wl_solve_params* prm)
 {
-    const auto t0 = std::chrono::steady_clock::now();
     if (!g) return set_error(WL_ERR_ARG, "NULL gauge object");
-    if (!x || !b || !prm || !info) return set_error(WL_ERR_ARG, "NULL pointer");
+    if (!x || !b || !prm) return set_error(WL_ERR_ARG, "NULL pointer");
     if (nrhs < 1 || nrhs > 65535) return set_error(WL_ERR_ARG, "nrhs must be in 1..65535");
     if (prm->inner < WL_F64 || prm->inner > WL_F16) return set_error(WL_ERR_ARG, "unknown inner precision");
     if (!(prm->tol > 0.0)) return set_error(WL_ERR_ARG, "tol must be > 0");
     if (prm->maxiter < 1) return set_error(WL_ERR_ARG, "maxiter must be >= 1");
     if (!g->links[prm->inner][0])
         return set_error(WL_ERR_STATE, "gauge object was created without the inner precision");
-    cudaStream_t s = (cudaStream_t)stream;
-    const int eo = prm->eo ? 1 : 0;
-    const int P = prm->inner;
+    return WL_OK;
+}
+
+int SolveState::begin(wl_gauge g_, double* x, const double* b, int nrhs_, const wl_solve_params* p,
+                      cudaStream_t s_)
+{
+    t0 = std::chrono::steady_clock::now();
+    WL_TRY(check_params(g_, x, b, nrhs_, p));
+    g = g_;
+    prm = p;
+    nrhs = nrhs_;
+    s = s_;
+    eo = p->eo ? 1 : 0;
+    P = p->inner;
+    x_user = x;
     WL_TRY(ensure_ws(g, P, nrhs, eo));
-    Workspace* w = g->ws;
+    w = g->ws;
     const long long V = 2 * g->geo.Vh;
-    const size_t canon = (size_t)V * 24 * sizeof(double) * nrhs;
+    canon = (size_t)V * 24 * sizeof(double) * nrhs;
 
     // host buffers are staged through the workspace
-    const bool host_b = is_host_pointer(b), host_x = is_host_pointer(x);
+    const bool host_b = is_host_pointer(b);
+    host_x = is_host_pointer(x);
     const double* bd = b;
-    double* xd = x;
+    xd = x;
     if (host_b || host_x) {
         if (w->stage_bytes < canon) {
             if (w->stage_b) cudaFree(w->stage_b);
@@ -744,52 +703,64 @@ extern "C" int wilson_solve(wl_gauge g, double* x, const double* b, int nrhs,
             xd = w->stage_x;
         }
     }
-
     const size_t hb64 = w->hb64;
-    const int nh = w->nhalf;
-    // b -> internal FP64 (even | odd per rhs); the conversion writes with the
-    // rhs stride of one half field, so convert each rhs separately
+    // b -> internal FP64 (even | odd per rhs); one conversion per rhs and parity
     for (int r = 0; r < nrhs; ++r) {
         char* dst = (char*)w->b64 + r * 2 * hb64;
         const double* src = bd + (size_t)r * V * 24;
-        WL_TRY(wl_field_to_internal(g, dst, src, 0, WL_F64, 1, s));
-        WL_TRY(wl_field_to_internal(g, dst + hb64, src, 1, WL_F64, 1, s));
+        WL_TRY(field_to_internal(g, dst, src, 0, WL_F64, 1, s));
+        WL_TRY(field_to_internal(g, dst + hb64, src, 1, WL_F64, 1, s));
         if (prm->use_x0) {
             char* xdst = (char*)w->xhi + r * 2 * hb64;
             const double* xs = xd + (size_t)r * V * 24;
-            WL_TRY(wl_field_to_internal(g, xdst, xs, 0, WL_F64, 1, s));
-            WL_TRY(wl_field_to_internal(g, xdst + hb64, xs, 1, WL_F64, 1, s));
+            WL_TRY(field_to_internal(g, xdst, xs, 0, w->outer, 1, s));
+            WL_TRY(field_to_internal(g, xdst + hb64, xs, 1, w->outer, 1, s));
         }
     }
     if (!prm->use_x0) WL_CUDA(cudaMemsetAsync(w->xhi, 0, 2 * hb64 * nrhs, s));
     // ||b||^2 over the full lattice
-    for (int k = 0; k < nrhs; ++k) w->mask_h[k] = 1;
-    WL_TRY(upload_mask(w, nrhs, s));
     WL_TRY(launch_cdot(g, WL_F64, w->b64, w->b64, 2, nrhs, w->nrm, 3, nullptr, s));
+    if (w->bout != w->b64)  // b in the outer precision
+        WL_TRY(launch_convert(g, w->outer, w->bout, WL_F64, w->b64, 2, nrhs, nullptr, s));
     WL_TRY(read_norms(w, nrhs, s));
-    std::vector<double> bnorm2(nrhs), rnorm2(nrhs), target2(nrhs);
+    bnorm2.assign(nrhs, 0.0);
+    rnorm2.assign(nrhs, 0.0);
+    target2.assign(nrhs, 0.0);
     for (int k = 0; k < nrhs; ++k) bnorm2[k] = w->nrm_h[3 * k + 2];
     // b' = b_e + kappa H_eo b_o (even-odd) or b (full)
     if (eo) {
         HopLaunch h;
-        h.prec = WL_F64;
+        h.prec = w->outer;
         h.parity0 = 0;
         h.nrhs = nrhs;
-        h.in[0] = (const char*)w->b64 + hb64;
+        h.in[0] = (const char*)w->bout + hb64;
         h.out[0] = w->bp;
-        h.x1[0] = w->b64;
+        h.x1[0] = w->bout;
         h.rs_in = h.rs_x1 = full_rs(w);
         h.rs_out = (long long)hb64;
         h.a = g->kappa;
+        if (g->has_clover) {  // b' = b_e + kappa H_eo A_oo^-1 b_o
+            WL_TRY(launch_clover_apply(g, w->outer, w->tmp64, (const char*)w->bout + hb64, 1, 1, nrhs, s,
+                                       (long long)hb64, full_rs(w)));
+            h.in[0] = w->tmp64;
+            h.rs_in = (long long)hb64;
+        }
         WL_TRY(launch_hop(g, h, s));
     } else {
-        WL_CUDA(cudaMemcpyAsync(w->bp, w->b64, 2 * hb64 * nrhs, cudaMemcpyDeviceToDevice, s));
+        WL_CUDA(cudaMemcpyAsync(w->bp, w->bout, 2 * hb64 * nrhs, cudaMemcpyDeviceToDevice, s));
     }
-    // state per rhs
-    std::vector<int> done(nrhs, 0), status(nrhs, WL_OK), outer(nrhs, 0), restarts(nrhs, 0);
+    done.assign(nrhs, 0);
+    final_target.assign(nrhs, 0);
+    shortcut.assign(nrhs, 0);
+    status.assign(nrhs, WL_OK);
+    outer.assign(nrhs, 0);
+    restarts.assign(nrhs, 0);
+    part.assign(nrhs, 0);
+    in_inner.assign(nrhs, 0);
+    poisoned.assign(nrhs, 0);
+    iters_before.assign(nrhs, 0);
     for (int k = 0; k < nrhs; ++k) {
         if (bnorm2[k] == 0.0) done[k] = 1;  // x = 0 solves b = 0 exactly
-        w->sc_h[k] = Scal();
         std::memset(&w->sc_h[k], 0, sizeof(Scal));
     }
     WL_CUDA(cudaMemcpyAsync(w->sc, w->sc_h, sizeof(Scal) * nrhs, cudaMemcpyHostToDevice, s));
@@ -798,163 +769,241 @@ extern "C" int wilson_solve(wl_gauge g, double* x, const double* b, int nrhs,
     if (prm->use_x0) {
         WL_TRY(residual64(g, w, nrhs, s));
     } else {  // x = 0: r = b' exactly, no FP64 matrix apply needed
-        WL_CUDA(cudaMemcpy2DAsync(w->rhi, w->vb64, w->bp, w->vb64, w->vb64, nrhs,
-                                  cudaMemcpyDeviceToDevice, s));
-        WL_TRY(launch_cdot(g, WL_F64, w->bp, w->bp, w->nhalf, nrhs, w->nrm, 3, w->mask, s));
+        WL_CUDA(cudaMemcpyAsync(w->rhi, w->bp, w->vb64 * nrhs, cudaMemcpyDeviceToDevice, s));
+        WL_TRY(launch_cdot(g, w->outer, w->bp, w->bp, w->nhalf, nrhs, w->nrm, 3, w->mask, s));
     }
     WL_TRY(read_norms(w, nrhs, s));
     for (int k = 0; k < nrhs; ++k) rnorm2[k] = w->mask_h[k] ? w->nrm_h[3 * k + 2] : 0.0;
 
-    const double delta2 = prm->delta > 0.0 ? prm->delta * prm->delta : 0.0;
-    const double inner_tol =
-        prm->inner_tol > 0.0 ? prm->inner_tol : (P == WL_F64 ? 0.0 : P == WL_F32 ? 1e-5 : 1e-3);
-    const int chunk = prm->graph_iters > 0 ? prm->graph_iters
-                      : prm->graph_iters < 0 ? -prm->graph_iters : 4;
-    const bool use_graph = prm->graph_iters > 0;
-    double safety = 0.5;  // aim below tol on the Schur residual; tightened if the true residual misses
-    int final_rounds = 0;
+    delta2 = prm->delta > 0.0 ? prm->delta * prm->delta : 0.0;
+    inner_tol = prm->inner_tol > 0.0 ? prm->inner_tol : (P == WL_F64 ? 0.0 : P == WL_F32 ? 1e-5 : 1e-3);
+    chunk = prm->graph_iters > 0 ? prm->graph_iters : prm->graph_iters < 0 ? -prm->graph_iters : 4;
+    use_graph = prm->graph_iters > 0;
+    safety = 0.5;  // aim below tol on the Schur residual; tightened if the true residual misses
+    final_rounds = 0;
+    return WL_OK;
+}
 
-    for (;;) {
-        // ---------------- outer loop: FP64 residual -> inner solve -> FP64 update
-        for (;;) {
-            int any = 0;
-            for (int k = 0; k < nrhs; ++k) {
-                if (done[k]) { w->mask_h[k] = 0; continue; }
-                const double goal2 = safety * safety * prm->tol * prm->tol * bnorm2[k];
-                if (rnorm2[k] <= goal2) { done[k] = 1; w->mask_h[k] = 0; continue; }
-                if (!std::isfinite(rnorm2[k])) { done[k] = 1; status[k] = WL_ERR_NAN; w->mask_h[k] = 0; continue; }
-                if (w->sc_h[k].iters >= prm->maxiter) { done[k] = 1; status[k] = WL_ERR_NOT_CONVERGED; w->mask_h[k] = 0; continue; }
-                w->mask_h[k] = 1;
-                any = 1;
-                double t2 = inner_tol * inner_tol * rnorm2[k];
-                if (delta2 > 0.0 || t2 < goal2) t2 = goal2;
-                target2[k] = t2;
+int SolveState::plan(bool* any_out)
+{
+    int any = 0;
+    for (int k = 0; k < nrhs; ++k) {
+        w->mask_h[k] = 0;
+        if (done[k]) continue;
+        const double goal2 = safety * safety * prm->tol * prm->tol * bnorm2[k];
+        if (rnorm2[k] <= goal2) { done[k] = 1; continue; }
+        if (!std::isfinite(rnorm2[k])) { done[k] = 1; status[k] = WL_ERR_NAN; continue; }
+        if (w->sc_h[k].iters >= prm->maxiter) { done[k] = 1; status[k] = WL_ERR_NOT_CONVERGED; continue; }
+        w->mask_h[k] = 1;
+        any = 1;
+        double t2 = inner_tol * inner_tol * rnorm2[k];
+        if (delta2 > 0.0 || t2 < goal2) t2 = goal2;
+        target2[k] = t2;
+        final_target[k] = t2 == goal2;
+        if (solve_verbose())
+            fprintf(stderr, "[wl solve] Vh=%lld rhs %d: round from iters %d, |r|/|b| %.3e, target %.3e%s\n",
+                    g->geo.Vh, k, w->sc_h[k].iters, std::sqrt(rnorm2[k] / bnorm2[k]),
+                    std::sqrt(t2 / bnorm2[k]), final_target[k] ? " (final)" : "");
+    }
+    *any_out = any != 0;
+    if (!any) return WL_OK;
+    for (int k = 0; k < nrhs; ++k) {
+        iters_before[k] = w->sc_h[k].iters;
+        part[k] = in_inner[k] = w->mask_h[k];
+        poisoned[k] = 0;
+    }
+    return inner_start(g, w, nrhs, target2.data(), delta2, s);
+}
+
+int SolveState::budget() const
+{
+    int most = 0;  // iterations done by the furthest-along right-hand side of the round
+    for (int k = 0; k < nrhs; ++k)
+        if (in_inner[k] && w->sc_h[k].iters > most) most = w->sc_h[k].iters;
+    return chunk < prm->maxiter - most ? chunk : prm->maxiter - most;
+}
+
+int SolveState::read_scalars()
+{
+    WL_CUDA(cudaMemcpyAsync(w->sc_h, w->sc, sizeof(Scal) * nrhs, cudaMemcpyDeviceToHost, s));
+    WL_CUDA(cudaStreamSynchronize(s));
+    return WL_OK;
+}
+
+int SolveState::after_chunk(bool* alive)
+{
+    int upd = 0, stopped = 0;
+    for (int k = 0; k < nrhs; ++k) {
+        w->mask_h[k] = 0;
+        if (!in_inner[k]) continue;
+        Scal& S = w->sc_h[k];
+        if (S.active && S.iters >= prm->maxiter) {
+            S.active = 0;  // pushed to the device below
+            S.flags |= FLAG_MAXITER;
+            stopped = 1;
+        }
+        if (S.active) {
+            if (S.want_update) { w->mask_h[k] = 1; upd = 1; }
+            continue;
+        }
+        in_inner[k] = 0;  // converged, out of iterations, or broke down
+        if (S.flags & (FLAG_BREAKDOWN | FLAG_NAN)) {
+            if (S.flags & FLAG_NAN) poisoned[k] = 1;
+            if (++restarts[k] > 5) {
+                done[k] = 1;
+                status[k] = (S.flags & FLAG_NAN) ? WL_ERR_NAN : WL_ERR_BREAKDOWN;
             }
-            if (!any) break;
-            std::vector<int> iters_before(nrhs);
-            for (int k = 0; k < nrhs; ++k) iters_before[k] = w->sc_h[k].iters;
-            WL_TRY(inner_start(g, w, nrhs, target2.data(), delta2, s));
-            std::vector<int> part(w->mask_h, w->mask_h + nrhs);  // took part in this round
-            std::vector<int> in_inner(part), poisoned(nrhs, 0);
-            for (;;) {
-                int most = 0;  // iterations done by the furthest-along active rhs
-                for (int k = 0; k < nrhs; ++k)
-                    if (in_inner[k] && w->sc_h[k].iters > most) most = w->sc_h[k].iters;
-                const int k_run = chunk < prm->maxiter - most ? chunk : prm->maxiter - most;
-                if (k_run <= 0) break;
-                WL_TRY(run_chunk(g, w, nrhs, k_run, use_graph && k_run == chunk, s));
-                WL_CUDA(cudaMemcpyAsync(w->sc_h, w->sc, sizeof(Scal) * nrhs, cudaMemcpyDeviceToHost, s));
-                WL_CUDA(cudaStreamSynchronize(s));
-                int upd = 0, stopped = 0;
-                for (int k = 0; k < nrhs; ++k) {
-                    w->mask_h[k] = 0;
-                    if (!in_inner[k]) continue;
-                    Scal& S = w->sc_h[k];
-                    if (S.active && S.iters >= prm->maxiter) {
-                        S.active = 0;  // pushed to the device below
-                        S.flags |= FLAG_MAXITER;
-                        stopped = 1;
-                    }
-                    if (S.active) {
-                        if (S.want_update) { w->mask_h[k] = 1; upd = 1; }
-                        continue;
-                    }
-                    in_inner[k] = 0;  // converged, out of iterations, or broke down
-                    if (S.flags & (FLAG_BREAKDOWN | FLAG_NAN)) {
-                        if (S.flags & FLAG_NAN) poisoned[k] = 1;
-                        if (++restarts[k] > 5) {
-                            done[k] = 1;
-                            status[k] = (S.flags & FLAG_NAN) ? WL_ERR_NAN : WL_ERR_BREAKDOWN;
-                        }
-                    }
-                }
-                if (stopped)
-                    WL_CUDA(cudaMemcpyAsync(w->sc, w->sc_h, sizeof(Scal) * nrhs, cudaMemcpyHostToDevice, s));
-                if (upd) {
-                    WL_TRY(reliable_update(g, w, nrhs, s));
-                    for (int k = 0; k < nrhs; ++k) if (w->mask_h[k]) outer[k]++;
-                    // refresh the host copy so later pushes keep the new scalars
-                    WL_CUDA(cudaMemcpyAsync(w->sc_h, w->sc, sizeof(Scal) * nrhs, cudaMemcpyDeviceToHost, s));
-                    WL_CUDA(cudaStreamSynchronize(s));
-                }
-                bool alive = false;
-                for (int k = 0; k < nrhs; ++k) alive |= in_inner[k] != 0;
-                if (!alive) break;
-            }
-            // x_hi += x_lo; r_hi = b' - A x_hi for every rhs that took part
-            int any_poison = 0;
-            for (int k = 0; k < nrhs; ++k) {
-                w->mask_h[k] = poisoned[k];
-                any_poison |= poisoned[k];
-            }
-            if (any_poison) {  // a NaN correction is dropped, not accumulated
-                WL_TRY(upload_mask(w, nrhs, s));
-                WL_TRY(launch_zero(g, w->xlo_prec, w->xlo, nh, nrhs, w->mask, s));
-            }
-            for (int k = 0; k < nrhs; ++k) w->mask_h[k] = part[k];
-            WL_TRY(upload_mask(w, nrhs, s));
-            WL_TRY(launch_accum_hi(g, w->xhi, w->xlo_prec, w->xlo, nh, nrhs, w->mask, s, full_rs(w)));
-            WL_TRY(residual64(g, w, nrhs, s));
-            WL_TRY(read_norms(w, nrhs, s));
+        }
+    }
+    if (stopped)
+        WL_CUDA(cudaMemcpyAsync(w->sc, w->sc_h, sizeof(Scal) * nrhs, cudaMemcpyHostToDevice, s));
+    if (upd) {
+        WL_TRY(reliable_update(g, w, nrhs, s));
+        for (int k = 0; k < nrhs; ++k) if (w->mask_h[k]) outer[k]++;
+        if (solve_verbose())
             for (int k = 0; k < nrhs; ++k)
-                if (part[k]) {
-                    rnorm2[k] = w->nrm_h[3 * k + 2];
-                    outer[k]++;
-                    // an inner solve that could not move (its start already met the
-                    // inner target) ends the outer loop; the true residual decides
-                    if (w->sc_h[k].iters == iters_before[k] && !done[k]) done[k] = 1;
-                    if (outer[k] > kMaxOuter && !done[k]) {
-                        done[k] = 1;
-                        status[k] = WL_ERR_NOT_CONVERGED;
-                    }
-                }
+                if (w->mask_h[k])
+                    fprintf(stderr, "[wl solve] Vh=%lld rhs %d: reliable update at iters %d\n", g->geo.Vh, k,
+                            w->sc_h[k].iters);
+        WL_TRY(read_scalars());  // keep the host copy current for later pushes
+    }
+    bool a = false;
+    for (int k = 0; k < nrhs; ++k) a |= in_inner[k] != 0;
+    *alive = a;
+    return WL_OK;
+}
+
+int SolveState::finish_round()
+{
+    const int nh = w->nhalf;
+    int any_poison = 0;
+    for (int k = 0; k < nrhs; ++k) {
+        w->mask_h[k] = poisoned[k];
+        any_poison |= poisoned[k];
+        in_inner[k] = 0;
+    }
+    if (any_poison) {  // a NaN correction is dropped, not accumulated
+        WL_TRY(upload_mask(w, nrhs, s));
+        WL_TRY(launch_zero(g, w->xlo_prec, w->xlo, nh, nrhs, w->mask, s));
+    }
+    for (int k = 0; k < nrhs; ++k) w->mask_h[k] = part[k];
+    WL_TRY(upload_mask(w, nrhs, s));
+    WL_TRY(launch_accum_hi(g, w->outer, w->xhi, w->xlo_prec, w->xlo, nh, nrhs, w->mask, s,
+                           full_rs(w)));
+    // a right-hand side whose inner solve just reached the final goal goes
+    // straight to the true-residual check; the others need the FP64 residual
+    int need = 0;
+    for (int k = 0; k < nrhs; ++k) {
+        const bool reached = part[k] && final_target[k] && !poisoned[k] &&
+                             (w->sc_h[k].flags & FLAG_CONVERGED) && w->sc_h[k].iters > iters_before[k];
+        if (reached) {
+            done[k] = 1;
+            shortcut[k] = 1;
+            outer[k]++;
+            part[k] = 0;
         }
-        // ---------------- reconstruct the odd half and check the true residual
-        if (eo) {
-            HopLaunch h;
-            h.prec = WL_F64;
-            h.parity0 = 1;
-            h.nrhs = nrhs;
-            h.in[0] = w->xhi;
-            h.out[0] = (char*)w->xhi + hb64;
-            h.x1[0] = (const char*)w->b64 + hb64;
-            h.rs_in = h.rs_out = h.rs_x1 = full_rs(w);
-            h.a = g->kappa;
-            WL_TRY(launch_hop(g, h, s));
-        }
-        WL_TRY(true_residual64(g, w, nrhs, s));
-        WL_TRY(read_norms(w, nrhs, s));
-        bool retry = false;
-        for (int k = 0; k < nrhs; ++k) {
-            const double tr = bnorm2[k] > 0 ? std::sqrt(w->nrm_h[3 * k + 2] / bnorm2[k]) : 0.0;
-            info[k].true_resid = tr;
-            if (status[k] == WL_OK && !(tr <= prm->tol)) {
-                if (final_rounds < 3 && w->sc_h[k].iters < prm->maxiter) {
-                    done[k] = 0;
-                    retry = true;
-                } else {
-                    status[k] = std::isfinite(tr) ? WL_ERR_NOT_CONVERGED : WL_ERR_NAN;
-                }
+        if (solve_verbose() && (reached || part[k]))
+            fprintf(stderr, "[wl solve] Vh=%lld rhs %d: round ends at iters %d, flags %d%s\n", g->geo.Vh, k,
+                    w->sc_h[k].iters, w->sc_h[k].flags, reached ? ", final goal reached: true residual next" : "");
+        w->mask_h[k] = part[k];
+        need |= part[k];
+    }
+    if (!need) return WL_OK;
+    WL_TRY(upload_mask(w, nrhs, s));
+    WL_TRY(residual64(g, w, nrhs, s));
+    WL_TRY(read_norms(w, nrhs, s));
+    for (int k = 0; k < nrhs; ++k)
+        if (part[k]) {
+            rnorm2[k] = w->nrm_h[3 * k + 2];
+            outer[k]++;
+            if (solve_verbose())
+                fprintf(stderr, "[wl solve] Vh=%lld rhs %d: outer residual %.3e\n", g->geo.Vh, k,
+                        std::sqrt(rnorm2[k] / bnorm2[k]));
+            // an inner solve that could not move (its start already met the
+            // inner target) ends the outer loop; the true residual decides
+            if (w->sc_h[k].iters == iters_before[k] && !done[k]) done[k] = 1;
+            if (outer[k] > kMaxOuter && !done[k]) {
+                done[k] = 1;
+                status[k] = WL_ERR_NOT_CONVERGED;
             }
         }
-        if (!retry) break;
-        // the Schur residual met the goal but the full one did not: aim lower
+    return WL_OK;
+}
+
+int SolveState::finalize(bool* retry_out)
+{
+    const size_t hb64 = w->hb64;
+    if (w->x64 != w->xhi)  // the solution in FP64 (the even half for even-odd solves)
+        WL_TRY(launch_convert(g, WL_F64, w->x64, w->outer, w->xhi, w->nhalf, nrhs, nullptr, s,
+                              full_rs(w), full_rs(w)));
+    if (eo) {  // x_o = b_o + kappa H_oe x_e in FP64
+        HopLaunch h;
+        h.prec = WL_F64;
+        h.parity0 = 1;
+        h.nrhs = nrhs;
+        h.in[0] = w->x64;
+        h.out[0] = (char*)w->x64 + hb64;
+        h.x1[0] = (const char*)w->b64 + hb64;
+        h.rs_in = h.rs_out = h.rs_x1 = full_rs(w);
+        h.a = g->kappa;
+        if (g->has_clover) {  // x_o = A_oo^-1 (b_o + kappa H_oe x_e)
+            h.cl_mode = kClOut;
+            h.clov[0] = g->clov[WL_F64][1][1];
+        }
+        WL_TRY(launch_hop(g, h, s));
+    }
+    WL_TRY(true_residual64(g, w, nrhs, s));
+    WL_TRY(read_norms(w, nrhs, s));
+    bool retry = false, tighten = false;
+    for (int k = 0; k < nrhs; ++k) {
+        const double tr = bnorm2[k] > 0 ? std::sqrt(w->nrm_h[3 * k + 2] / bnorm2[k]) : 0.0;
+        rnorm2[k] = tr;  // kept for end(); overwritten below on retry
+        if (solve_verbose())
+            fprintf(stderr, "[wl solve] Vh=%lld rhs %d: true residual %.3e at iters %d (shortcut %d)\n",
+                    g->geo.Vh, k, tr, w->sc_h[k].iters, shortcut[k]);
+        if (status[k] == WL_OK && !(tr <= prm->tol)) {
+            if (shortcut[k]) {
+                // only the iterated residual had met the goal: run another round
+                // from the FP64 residual at the same goal
+                shortcut[k] = 0;
+                done[k] = 0;
+                retry = true;
+            } else if (final_rounds < 3 && w->sc_h[k].iters < prm->maxiter) {
+                done[k] = 0;
+                retry = tighten = true;
+            } else {
+                status[k] = std::isfinite(tr) ? WL_ERR_NOT_CONVERGED : WL_ERR_NAN;
+            }
+        } else {
+            shortcut[k] = 0;
+        }
+    }
+    true_resid.assign(rnorm2.begin(), rnorm2.end());
+    *retry_out = retry;
+    if (!retry) return WL_OK;
+    if (tighten) {  // the FP64 Schur residual met the goal but the full one did not: aim lower
         ++final_rounds;
         safety *= 0.1;
-        for (int k = 0; k < nrhs; ++k) w->mask_h[k] = done[k] ? 0 : 1;
-        WL_TRY(upload_mask(w, nrhs, s));
-        WL_TRY(residual64(g, w, nrhs, s));
-        WL_TRY(read_norms(w, nrhs, s));
-        for (int k = 0; k < nrhs; ++k) if (w->mask_h[k]) rnorm2[k] = w->nrm_h[3 * k + 2];
     }
-    // x -> canonical
+    for (int k = 0; k < nrhs; ++k) w->mask_h[k] = done[k] ? 0 : 1;
+    WL_TRY(upload_mask(w, nrhs, s));
+    WL_TRY(residual64(g, w, nrhs, s));
+    WL_TRY(read_norms(w, nrhs, s));
+    for (int k = 0; k < nrhs; ++k) if (w->mask_h[k]) rnorm2[k] = w->nrm_h[3 * k + 2];
+    return WL_OK;
+}
+
+int SolveState::end(wl_solve_info* info)
+{
+    const size_t hb64 = w->hb64;
+    const long long V = 2 * g->geo.Vh;
     for (int r = 0; r < nrhs; ++r) {
-        const char* src = (const char*)w->xhi + r * 2 * hb64;
+        const char* src = (const char*)w->x64 + r * 2 * hb64;
         double* dst = xd + (size_t)r * V * 24;
-        WL_TRY(wl_field_to_canonical(g, dst, src, 0, WL_F64, 1, s));
-        WL_TRY(wl_field_to_canonical(g, dst, src + hb64, 1, WL_F64, 1, s));
+        WL_TRY(field_to_canonical(g, dst, src, 0, WL_F64, 1, s));
+        WL_TRY(field_to_canonical(g, dst, src + hb64, 1, WL_F64, 1, s));
     }
-    if (host_x) WL_CUDA(cudaMemcpyAsync(x, xd, canon, cudaMemcpyDeviceToHost, s));
+    if (host_x) WL_CUDA(cudaMemcpyAsync(x_user, xd, canon, cudaMemcpyDeviceToHost, s));
     WL_CUDA(cudaStreamSynchronize(s));
     const double secs =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -964,6 +1013,7 @@ extern "C" int wilson_solve(wl_gauge g, double* x, const double* b, int nrhs,
         info[k].outer = outer[k];
         info[k].restarts = restarts[k];
         info[k].status = status[k];
+        info[k].true_resid = true_resid.empty() ? 0.0 : true_resid[k];
         info[k].secs = secs;
         if (status[k] != WL_OK && rc == WL_OK) rc = status[k];
     }
@@ -971,18 +1021,36 @@ extern "C" int wilson_solve(wl_gauge g, double* x, const double* b, int nrhs,
     return rc;
 }
 
-extern "C" int wilson_solve_batch(int nlat, const wl_gauge* gs, double* const* x,
-                                  const double* const* b, const int* nrhs,
-                                  const wl_solve_params* p, wl_solve_info* info, void* stream)
+}  // namespace wl
+
+using namespace wl;
+
+extern "C" int wilson_solve(wl_gauge g, double* x, const double* b, int nrhs,
+                            const wl_solve_params* prm, wl_solve_info* info, void* stream)
 {
-    if (nlat < 1 || !gs || !x || !b || !nrhs || !p || !info)
-        return set_error(WL_ERR_ARG, "bad batch arguments");
-    int rc = WL_OK, off = 0;
-    for (int l = 0; l < nlat; ++l) {
-        const int r = wilson_solve(gs[l], x[l], b[l], nrhs[l], p, info + off, stream);
-        if (r != WL_OK && rc == WL_OK) rc = r;
-        if (r == WL_ERR_ARG || r == WL_ERR_CUDA || r == WL_ERR_STATE) return r;
-        off += nrhs[l];
+    WL_ENTRY();
+    if (!info) return set_error(WL_ERR_ARG, "NULL pointer");
+    SolveState st;
+    WL_TRY(st.begin(g, x, b, nrhs, prm, (cudaStream_t)stream));
+    for (;;) {
+        for (;;) {  // outer loop: FP64 residual -> inner solve -> FP64 update
+            bool any = false;
+            WL_TRY(st.plan(&any));
+            if (!any) break;
+            for (;;) {
+                const int k = st.budget();
+                if (k <= 0) break;
+                WL_TRY(run_chunk(g, st.w, nrhs, k, st.use_graph && k == st.chunk, st.s));
+                WL_TRY(st.read_scalars());
+                bool alive = false;
+                WL_TRY(st.after_chunk(&alive));
+                if (!alive) break;
+            }
+            WL_TRY(st.finish_round());
+        }
+        bool retry = false;
+        WL_TRY(st.finalize(&retry));
+        if (!retry) break;
     }
-    return rc;
+    return st.end(info);
 }

@@ -17,8 +17,8 @@ import torch
 
 from . import build as _build
 
-WL_F64, WL_F32, WL_F16 = 0, 1, 2
-PREC = {"f64": WL_F64, "f32": WL_F32, "f16": WL_F16}
+WL_F64, WL_F32, WL_F16, WL_DF64 = 0, 1, 2, 3
+PREC = {"f64": WL_F64, "f32": WL_F32, "f16": WL_F16, "df64": WL_DF64}
 WL_OK, WL_ERR_ARG, WL_ERR_CUDA, WL_ERR_NOT_CONVERGED = 0, -1, -2, -3
 WL_ERR_BREAKDOWN, WL_ERR_NAN, WL_ERR_TIMEOUT, WL_ERR_STATE = -4, -5, -6, -7
 ERR_NAMES = {0: "WL_OK", -1: "WL_ERR_ARG", -2: "WL_ERR_CUDA", -3: "WL_ERR_NOT_CONVERGED",
@@ -83,6 +83,8 @@ def load() -> ctypes.CDLL:
             "wl_field_to_canonical": (I, [P, P, P, I, I, I, P]),
             "wilson_dslash": (I, [P, P, P, I, I, I, I, P]),
             "wilson_mult": (I, [P, P, P, I, I, I, I, P]),
+            "wl_clover_set": (I, [P, P, P]),
+            "wl_clover_apply": (I, [P, P, P, I, I, I, I, P]),
             "wl_cdot": (I, [P, P, P, P, I, I, P]),
             "wl_cdot_noalloc": (I, [P, P, P, LL, I, I, P]),
             "wilson_solve": (I, [P, P, P, I, ctypes.POINTER(wl_solve_params),
@@ -107,7 +109,7 @@ def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["wl_gauge_create", "wl_gauge_destroy", "wl_half_volume", "wl_field_bytes",
             "wl_field_to_internal", "wl_field_to_canonical", "wilson_dslash", "wilson_mult",
-            "wl_cdot", "wl_cdot_noalloc", "wilson_solve", "wilson_solve_batch", "wl_last_error",
+            "wl_clover_set", "wl_clover_apply", "wl_cdot", "wl_cdot_noalloc", "wilson_solve", "wilson_solve_batch", "wl_last_error",
             "wl_launch_count", "wl_algorithmic_bytes", "wl_timing", "wl_timing_read"]
 
 
@@ -184,6 +186,17 @@ def wilson_dslash(g, out, inp, out_parity: int, dagger: int, prec: int, nrhs: in
 def wilson_mult(g, out, inp, eo: int, dagger: int, prec: int, nrhs: int, stream=None) -> None:
     _check(load().wilson_mult(g, _ptr(out), _ptr(inp), int(eo), int(dagger), int(prec),
                               int(nrhs), _stream(stream)))
+
+
+def wl_clover_set(g, F, stream=None) -> None:
+    """Attach the clover term F (device FP64 [V][2][6][6] complex; None detaches)."""
+    _check(load().wl_clover_set(g, _ptr(F), _stream(stream)))
+
+
+def wl_clover_apply(g, out, inp, parity: int, inverse: int, prec: int, nrhs: int,
+                    stream=None) -> None:
+    _check(load().wl_clover_apply(g, _ptr(out), _ptr(inp), int(parity), int(inverse), int(prec),
+                                  int(nrhs), _stream(stream)))
 
 
 def wl_cdot(g, out, a, b, prec: int, nrhs: int, stream=None) -> None:

@@ -56,7 +56,7 @@ def full_canonical(c, internal, prec, nrhs):
 # a1: layout conversion
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df64"])
 def test_conversion_round_trip(case, prec):
     psi = case.source(nrhs=2, seed=11)
     for p in (0, 1):
@@ -72,14 +72,14 @@ def test_conversion_round_trip(case, prec):
         if prec == "f64":
             assert err == 0.0
         else:
-            assert err < {"f32": 1e-7, "f16": 1.3e-3}[prec], err
+            assert err < {"f32": 1e-7, "f16": 1.3e-3, "df64": 1e-14}[prec], err
 
 
 # ----------------------------------------------------------------------------
 # a2: hopping term
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df64"])
 @pytest.mark.parametrize("dagger", [0, 1])
 def test_dslash_matches_oracle(case, prec, dagger):
     nrhs = 2
@@ -113,7 +113,7 @@ def test_dslash_rejects_overlap_and_bad_args(case):
 # a3: matrix applies
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df64"])
 @pytest.mark.parametrize("dagger", [0, 1])
 def test_full_D_matches_oracle(case, prec, dagger):
     nrhs = 2
@@ -128,7 +128,7 @@ def test_full_D_matches_oracle(case, prec, dagger):
         assert rel(got[r], want) < TOL[prec], (prec, r)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df64"])
 @pytest.mark.parametrize("dagger", [0, 1])
 def test_Mee_matches_oracle(case, prec, dagger):
     nrhs = 3
@@ -147,7 +147,7 @@ def test_Mee_matches_oracle(case, prec, dagger):
 # a5: reductions
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df64"])
 def test_cdot_matches_oracle(case, prec):
     nrhs = 3
     a = case.source(nrhs=nrhs, seed=51)
@@ -159,7 +159,7 @@ def test_cdot_matches_oracle(case, prec):
     # the oracle reduces the fields as the library stores them
     ca = case.to_canonical(ia, 0, prec, nrhs)
     cb = case.to_canonical(ib, 0, prec, nrhs)
-    tol = {"f64": 1e-13, "f32": 1e-6, "f16": 1e-6}[prec]
+    tol = {"f64": 1e-13, "f32": 1e-6, "f16": 1e-6, "df64": 1e-13}[prec]
     for r in range(nrhs):
         ha, hb = case.half(ca, 0, r), case.half(cb, 0, r)
         d = oracle.cdot(ha, hb)
