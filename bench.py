@@ -43,7 +43,8 @@ UNIT = "GB/s"
 FALLBACK_HBM_GBS = 6800.0
 WORKLOAD_INDEX = 1  # 32^3x64 even-odd, FP32 inner, FP64 defect correction
 PROFILE = os.path.join(ROOT, "profiles", "hop_f32_32x32x32x64.md")
-KERNEL_SOURCES = ["paper_1811_00893_gb300/csrc/dslash.cu", "paper_1811_00893_gb300/csrc/hop.cuh",
+KERNEL_SOURCES = ["paper_1811_00893_gb300/csrc/dslash.cu", "paper_1811_00893_gb300/csrc/hop_kernels.cuh",
+                  "paper_1811_00893_gb300/csrc/hop.cuh", "paper_1811_00893_gb300/csrc/clover.cuh",
                   "paper_1811_00893_gb300/csrc/common.cuh", "paper_1811_00893_gb300/csrc/df64.cuh"]
 
 
@@ -235,8 +236,12 @@ def config_of(wl):
     from paper_1811_00893_gb300 import costs
     prec, kw = SCHEMES[wl.scheme]
     links = costs.link_bytes(prec) * 8 * wl.volume  # both parities
-    return {"workload": wl.name + f", kappa={wl.kappa}, {wl.links} links, {wl.nrhs} Gaussian "
-                                  f"RHS, to 1e-10 true residual",
+    extra = {}
+    if wl.clover:
+        extra["clover"] = ("synthetic F(x): two random Hermitian 6x6 blocks per site, scale 0.1, "
+                           f"seed {wl.clover_seed}")
+    return {**{"workload": wl.name + f", kappa={wl.kappa}, {wl.links} links, {wl.nrhs} Gaussian "
+                                     f"RHS, to 1e-10 true residual"}, **extra,
             "dims": list(wl.dims), "kappa": wl.kappa, "bc": "periodic xyz, antiperiodic t",
             "nrhs": wl.nrhs, "tol": 1e-10, "inner": prec, "outer": "f64", "scheme": wl.scheme,
             "seeds": {"gauge": wl.gauge_seed, "source": wl.source_seed},
@@ -245,27 +250,38 @@ def config_of(wl):
                    f"inputs smaller than L2 ({links / 1e6:.1f} MB of links): cache-resident")}
 
 
-def oracle_sample(wl, U_host, b_host, seconds: float):
-    """Time the FP64 oracle's even-odd BiCGStab on this lattice for about
-    `seconds`; returns (GB/s of algorithmic traffic, cores, description)."""
+def oracle_sample(wl, U_host, b_host, seconds: float, F_host=None):
+    """Time the FP64 oracle's BiCGStab (even-odd or full, Wilson or clover) on
+    this lattice for about `seconds`; returns (GB/s of algorithmic traffic,
+    cores, description, seconds per iteration)."""
     import oracle
     from paper_1811_00893_gb300 import costs
     oracle.build()
+    clover = F_host is not None
     if wl.eo:
         be, bo = oracle.split(b_host, wl.dims)
+        if clover:  # b' = b_e + kappa H_eo A_oo^-1 b_o
+            bo = oracle.clover_diag(F_host, bo, wl.dims, 1, inverse=True)
         bsys = be + wl.kappa * oracle.hop_eo(U_host, bo, wl.dims, wl.bc, 0)
     else:
         bsys = b_host
+
+    def iterate(n):
+        if clover:
+            oracle.clover_bicgstab_fixed(U_host, F_host, bsys, wl.dims, wl.bc, wl.kappa, wl.eo, n)
+        else:
+            oracle.bicgstab_fixed(U_host, bsys, wl.dims, wl.bc, wl.kappa, wl.eo, n)
+
     t0 = time.perf_counter()
-    oracle.bicgstab_fixed(U_host, bsys, wl.dims, wl.bc, wl.kappa, wl.eo, 1)
+    iterate(1)
     t1 = time.perf_counter() - t0
     n = int(max(1, min(60, seconds / max(t1, 1e-3))))
     t0 = time.perf_counter()
-    oracle.bicgstab_fixed(U_host, bsys, wl.dims, wl.bc, wl.kappa, wl.eo, n)
+    iterate(n)
     dt = time.perf_counter() - t0
     sites = wl.volume // 2 if wl.eo else wl.volume
-    per_iter = costs.bicgstab_iteration_bytes("f64", "f64", eo=wl.eo) * sites
-    kind = "even-odd" if wl.eo else "full-D"
+    per_iter = costs.bicgstab_iteration_bytes("f64", "f64", eo=wl.eo, clover=clover) * sites
+    kind = ("even-odd" if wl.eo else "full-D") + (" clover" if clover else "")
     return (n * per_iter / dt / 1e9, oracle.get_threads(),
             f"{n} FP64 {kind} BiCGStab iterations of the oracle (one right-hand side) on the "
             f"full {'x'.join(map(str, wl.dims))} lattice ({dt:.1f} s), bytes counted with the "
@@ -278,13 +294,13 @@ def oracle_sample(wl, U_host, b_host, seconds: float):
 
 def run_ours(args, rank, world, local):
     import torch
-    from paper_1811_00893_gb300 import costs, wilson
-    from paper_1811_00893_gb300.workloads import WORKLOADS
+    from paper_1811_00893_gb300 import costs, fields, wilson
+    from paper_1811_00893_gb300.workloads import by_index
 
     torch.cuda.set_device(local)
     dist_init(world, "nccl")
     dev = f"cuda:{local}"
-    wl = WORKLOADS[args.workload]
+    wl = by_index(args.workload)
     if args.dims:
         import dataclasses
         wl = dataclasses.replace(wl, dims=tuple(int(v) for v in args.dims.split(",")))
@@ -296,6 +312,12 @@ def run_ours(args, rank, world, local):
     b_host = b[0].cpu().numpy() if want_cpu else None
     g = wilson.Gauge(wl.dims, wl.kappa, U, precs=("f64", pname), bc=wl.bc)
     del U
+    F_host = None
+    if wl.clover:  # D_clov of Eq. 2: attach the seeded synthetic clover field
+        F = fields.clover_field(wl.dims, wl.clover_seed, device=dev)
+        wilson.wl_clover_set(g.handle, F)
+        F_host = F.cpu().numpy() if want_cpu else None
+        del F
     torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
     x = torch.zeros_like(b)
@@ -372,6 +394,21 @@ def run_ours(args, rank, world, local):
               "gflops": costs.FLOPS_HOP_SITE * Vh * nr / dslash_s / 1e9,
               "us_per_launch": dslash_s * 1e6, "frac_hbm": dslash_gbs / peak,
               "bytes_per_site": bps, "launches": 1000}
+    if wl.clover:  # the fused clover Schur apply: A_oo^-1 H_oe, then A_ee in - k^2 H_eo tmp
+        for _ in range(5):
+            wilson.wilson_mult(g.handle, fout, fin, 1, 0, P, nr)
+        torch.cuda.synchronize()
+        d0.record(stream)
+        for _ in range(200):
+            wilson.wilson_mult(g.handle, fout, fin, 1, 0, P, nr)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        mult_s = d0.elapsed_time(d1) / 1e3 / 200
+        mbps = (costs.hop_bytes_per_site(pname, nrhs=nr, clover=True) +
+                costs.hop_bytes_per_site(pname, nrhs=nr, extra_in=1, clover=True))
+        dslash["clover_mee"] = {"gbs": mbps * Vh / mult_s / 1e9, "us_per_apply": mult_s * 1e6,
+                                "bytes_per_site": mbps, "frac_hbm": mbps * Vh / mult_s / 1e9 / peak,
+                                "launches_per_apply": 2}
 
     # ---------------- plain FP64 GPU solve for the time-to-solution comparison
     x64 = torch.zeros_like(b)
@@ -400,13 +437,16 @@ def run_ours(args, rank, world, local):
                     "d2h_bytes_per_step": nbytes_io, "ms_per_step": e2e_ms,
                     "timer": "wall clock around wilson_solve with pinned host b and x"},
             "gpu_launches": launches,
+            # library launch-counter values around the timed region: launches
+            # [l0, l1) of this process's library kernels are the timed ones
+            "launch_index_range": [l0, l0 + launches],
             "roofline": {"kernel": (f"hop_kernel<{pname}>" if nr == 1 else
                                     f"hop_mrhs_kernel<{pname}>") +
                                    " (all hopping launches of the inner solve)",
                          "bound": "alu" if P == wilson.WL_F64 else "hbm", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,
-                         "traffic": traffic if (P == wilson.WL_F32 and nr == 1
+                         "traffic": traffic if (P == wilson.WL_F32 and nr == 1 and not wl.clover
                                                 and wl.dims == (32, 32, 32, 64)) else None,
                          "launches": hop_n,
                          "algorithmic_bytes_per_launch": hop_bytes / max(hop_n, 1),
@@ -423,7 +463,8 @@ def run_ours(args, rank, world, local):
                       "fp64_true_resid": max(i["true_resid"] for i in info64)},
         }
         if want_cpu:
-            gbs, cores, sample, s_per_iter = oracle_sample(wl, U_host, b_host, args.cpu_seconds)
+            gbs, cores, sample, s_per_iter = oracle_sample(wl, U_host, b_host, args.cpu_seconds,
+                                                           F_host)
             out["cpu_baseline"] = {"value": gbs, "unit": UNIT, "cores": cores, "kind": "oracle",
                                    "sample": sample, "seconds_per_iteration": s_per_iter}
         else:
@@ -532,9 +573,9 @@ def run_reference(args, rank, world, local):
 
     import oracle
     from paper_1811_00893_gb300 import costs
-    from paper_1811_00893_gb300.workloads import WORKLOADS
+    from paper_1811_00893_gb300.workloads import by_index
 
-    wl = WORKLOADS[WORKLOAD_INDEX]
+    wl = by_index(WORKLOAD_INDEX)
     dev = f"cuda:{local}" if torch.cuda.is_available() else "cpu"
     U, b = make_inputs(wl, 0, dev)  # same seeded inputs as the GPU arm
     U_host, b_host = U.cpu().numpy(), b[0].cpu().numpy()

@@ -58,23 +58,40 @@ def link_bytes(prec: str) -> int:
     return LINK_REALS * WORD[prec]
 
 
-def hop_bytes_per_site(prec: str, nrhs: int = 1, extra_in: int = 0, extra_out: int = 0) -> int:
+#: reals of the clover term per site (Eq. 2): two Hermitian 6x6 blocks = 2 x 36
+CLOVER_REALS = 72
+
+
+def clover_bytes(prec: str) -> int:
+    """Bytes of the packed clover matrix (A = 1 + F or its inverse) per site;
+    288 in single precision, Table 1's clover surplus over the Wilson matrix."""
+    return CLOVER_REALS * WORD[prec]
+
+
+def hop_bytes_per_site(prec: str, nrhs: int = 1, extra_in: int = 0, extra_out: int = 0,
+                       clover: bool = False) -> int:
     """Algorithmic bytes per output site of one even-odd hopping kernel:
-    eight links read once for all right-hand sides, one input spinor and one
-    output spinor per right-hand side, plus `extra_in` / `extra_out` fused
-    epilogue fields per right-hand side."""
-    return 8 * link_bytes(prec) + nrhs * (1 + extra_in + 1 + extra_out) * spinor_bytes(prec)
+    eight links (and, with the clover term fused, one clover matrix) read
+    once for all right-hand sides, one input spinor and one output spinor per
+    right-hand side, plus `extra_in` / `extra_out` fused epilogue fields per
+    right-hand side."""
+    return (8 * link_bytes(prec) + (clover_bytes(prec) if clover else 0) +
+            nrhs * (1 + extra_in + 1 + extra_out) * spinor_bytes(prec))
 
 
-def bicgstab_iteration_bytes(prec: str, xprec: str, eo: bool = True) -> int:
+def bicgstab_iteration_bytes(prec: str, xprec: str, eo: bool = True, clover: bool = False) -> int:
     """Algorithmic bytes per site of one BiCGStab iteration as this library
     schedules it (per half-lattice site for eo, per lattice site for the full
     D).  Matrix applies: M_ee is two hopping launches, the first writing an
     odd temporary (links, in, out) and the second fusing the xpay and the dot
     (links, in, out, x1, w); the full D is one launch per apply that fuses
     both (links, in, out, x1, w).  Vector passes: p update 4 fields, s update
-    3, x/r update 5 plus reading and writing x."""
+    3, x/r update 5 plus reading and writing x.  With the clover term each
+    hopping launch also reads one clover matrix per output site (A_oo^-1,
+    then A_ee for M_ee; A for the full D)."""
     sp, lk, xb = spinor_bytes(prec), 8 * link_bytes(prec), spinor_bytes(xprec)
+    if clover:
+        lk += clover_bytes(prec)
     if eo:
         applies = 2 * ((lk + 2 * sp) + (lk + 4 * sp))
     else:
