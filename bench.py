@@ -41,6 +41,7 @@ if ROOT not in sys.path:
 METRIC = "Dslash GB/s & GFlop/s (% HBM peak); mixed vs FP64 solve time to 1e-10 residual"
 UNIT = "GB/s"
 FALLBACK_HBM_GBS = 6800.0
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 non-tensor FP64, nominal
 WORKLOAD_INDEX = 1  # 32^3x64 even-odd, FP32 inner, FP64 defect correction
 PROFILE = os.path.join(ROOT, "profiles", "hop_f32_32x32x32x64.md")
 KERNEL_SOURCES = ["paper_1811_00893_gb300/csrc/dslash.cu", "paper_1811_00893_gb300/csrc/hop_kernels.cuh",
@@ -426,6 +427,34 @@ def run_ours(args, rank, world, local):
     if rank == 0:
         achieved = hop_bytes / (hop_ms / 1e3) / 1e9 if hop_ms > 0 else None
         traffic = profiled_traffic()
+        kname = f"hop_kernel<{pname}>" if nr == 1 else f"hop_mrhs_kernel<{pname}>"
+        if P == wilson.WL_F64:
+            # FP64 arithmetic bounds the FP64 stencil on GB300; no measured FP64
+            # peak exists, so the nominal rate is the denominator
+            tf = dslash["gflops"] / 1e3
+            roofline = {"kernel": kname + " (1000-launch protocol)", "bound": "alu", "achieved": tf,
+                        "peak": FP64_NOMINAL_TFLOPS, "peak_kind": "nominal FP64 rate of GB300",
+                        "unit": "TFLOP/s", "frac": tf / FP64_NOMINAL_TFLOPS, "traffic": None,
+                        "launches": 1000, "avg_us": dslash["us_per_launch"]}
+        elif hop_n == 0:
+            # the solve's hopping launches run inside CUDA graphs, which the
+            # per-launch timer does not see: report the kernel timed alone
+            roofline = {"kernel": kname + " (1000-launch protocol; the solve replays it in CUDA graphs)",
+                        "bound": "hbm", "achieved": dslash_gbs, "peak": peak, "peak_kind": peak_kind,
+                        "unit": "GB/s", "frac": dslash_gbs / peak, "traffic": None, "launches": 1000,
+                        "algorithmic_bytes_per_launch": bps * Vh, "avg_us": dslash["us_per_launch"]}
+        else:
+            roofline = {"kernel": kname + " (all hopping launches of the inner solve)",
+                        "bound": "hbm", "achieved": achieved, "peak": peak,
+                        "peak_kind": peak_kind, "unit": "GB/s",
+                        "frac": (achieved / peak) if achieved else None,
+                        "traffic": traffic if (P == wilson.WL_F32 and nr == 1 and not wl.clover
+                                               and wl.dims == (32, 32, 32, 64)) else None,
+                        "launches": hop_n,
+                        "algorithmic_bytes_per_launch": hop_bytes / max(hop_n, 1),
+                        "avg_us": hop_ms * 1e3 / max(hop_n, 1),
+                        "share_of_step": hop_ms / ms_local if ms_local else None,
+                        "f64_hop_share_of_step": h64_ms / ms_local if ms_local else None}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_per_step,
@@ -440,19 +469,7 @@ def run_ours(args, rank, world, local):
             # library launch-counter values around the timed region: launches
             # [l0, l1) of this process's library kernels are the timed ones
             "launch_index_range": [l0, l0 + launches],
-            "roofline": {"kernel": (f"hop_kernel<{pname}>" if nr == 1 else
-                                    f"hop_mrhs_kernel<{pname}>") +
-                                   " (all hopping launches of the inner solve)",
-                         "bound": "alu" if P == wilson.WL_F64 else "hbm", "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None,
-                         "traffic": traffic if (P == wilson.WL_F32 and nr == 1 and not wl.clover
-                                                and wl.dims == (32, 32, 32, 64)) else None,
-                         "launches": hop_n,
-                         "algorithmic_bytes_per_launch": hop_bytes / max(hop_n, 1),
-                         "avg_us": hop_ms * 1e3 / max(hop_n, 1),
-                         "share_of_step": hop_ms / ms_local if ms_local else None,
-                         "f64_hop_share_of_step": h64_ms / ms_local if ms_local else None},
+            "roofline": roofline,
             "dslash": dslash,
             "solve": {"mixed_ms": ms_per_step, "fp64_ms": fp64_ms,
                       "speedup_vs_fp64": fp64_ms / ms_per_step,

@@ -65,7 +65,7 @@ def build(force: bool = False, extra=(), verbose: bool = False) -> str:
     if not force and not extra and up_to_date():
         return LIB
     os.makedirs(OBJ, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(lambda s: compile_unit(s, extra), sources()))
     tmp = LIB + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]

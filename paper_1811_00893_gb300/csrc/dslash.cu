@@ -14,7 +14,7 @@
 
 namespace wl {
 
-// the clover variants are instantiated in dslash_clover.cu
+// the clover variants are instantiated in dslash_clover_x2.cu and dslash_clover_out.cu
 extern template struct HopKernels<kClX2>;
 extern template struct HopKernels<kClOut>;
 
@@ -43,6 +43,27 @@ static void launch_multi(const HopLaunch& h, const HopArgs& A, int nrhs, dim3 gr
     }
 }
 
+static void launch_pipe(const HopLaunch& h, const HopArgs& A, int nrhs, int ntiles, dim3 grid,
+                        dim3 block, size_t smem, cudaStream_t s)
+{
+    switch (h.cl_mode) {
+        case kClX2: HopKernels<kClX2>::pipe(h.prec, h.dagger, h.dot, A, nrhs, ntiles, grid, block, smem, s); break;
+        case kClOut: HopKernels<kClOut>::pipe(h.prec, h.dagger, h.dot, A, nrhs, ntiles, grid, block, smem, s); break;
+        default: HopKernels<kClNone>::pipe(h.prec, h.dagger, h.dot, A, nrhs, ntiles, grid, block, smem, s); break;
+    }
+}
+
+static const void* pipe_kernel(const HopLaunch& h)
+{
+    return h.cl_mode == kClX2    ? HopKernels<kClX2>::pipe_kernel(h.prec, h.dagger, h.dot)
+           : h.cl_mode == kClOut ? HopKernels<kClOut>::pipe_kernel(h.prec, h.dagger, h.dot)
+                                 : HopKernels<kClNone>::pipe_kernel(h.prec, h.dagger, h.dot);
+}
+
+// Multi-RHS launch shapes: 1..8 = right-hand-side lanes (warps) of
+// hop_mrhs_kernel; kPipeShape + lanes = the pipelined persistent kernel.
+static const int kPipeShape = 16;
+
 // Resident-block grid of the reducing single-RHS hop kernel.
 static int single_grid_cap(const HopLaunch& h, int block)
 {
@@ -66,6 +87,15 @@ static int launch_shape(const HopLaunch& h, HopArgs& A, int nrhs, int shape, cud
     if (!multi) {
         if (h.dot) gx = std::min(gx, (unsigned)single_grid_cap(h, shape));
         launch_single(h, A, dim3(gx, 1), shape, s);
+    } else if (shape > kPipeShape) {
+        const dim3 block(kTile, shape - kPipeShape);
+        const size_t smem = 2 * link_field_bytes(h.prec, kTile) + sizeof(double) * 3 * nrhs;
+        const int ntiles = (int)gx;
+        const int grid = std::min(ntiles, resident_grid(pipe_kernel(h), kTile * (shape - kPipeShape), smem));
+        launch_pipe(h, A, nrhs, ntiles, dim3((unsigned)grid), block, smem, s);
+        if (h.dot)  // per-tile partials, added in tile order
+            return launch_finish_slots(A.red.partial, (long long)A.red.max_blocks * 3, ntiles, nrhs,
+                                       A.dot_out, A.dot_stride, A.active, A.active_stride, s);
     } else {
         const dim3 block(kTile, shape);
         const size_t smem = link_field_bytes(h.prec, kTile) + sizeof(double) * 3 * nrhs;
@@ -111,12 +141,24 @@ static int tuned_shape(wl_gauge g, const HopLaunch& h, HopArgs& A, int nrhs, cud
             *shape = v;
             return WL_OK;
         }
+    } else {  // explicit override of the multi-RHS shape (for sweeps and tests)
+        const char* fs = getenv("WL_MRHS_SHAPE");
+        const int v = fs ? atoi(fs) : 0;
+        const bool narrow = h.prec == WL_F32 || h.prec == WL_F16;
+        if ((v >= 1 && v <= 8 && v <= nrhs) ||
+            (narrow && v > kPipeShape && v <= kPipeShape + 8 && v - kPipeShape <= nrhs)) {
+            *shape = v;
+            return WL_OK;
+        }
     }
     if (!autotune_enabled() || is_capturing(s)) return WL_OK;
     std::vector<int> cand;
     if (multi) {
         for (int l : {1, 2, 4, 8})
             if (l <= nrhs) cand.push_back(l);
+        if (h.prec == WL_F32 || h.prec == WL_F16)
+            for (int l : {2, 4, 8})
+                if (l <= nrhs) cand.push_back(kPipeShape + l);
     } else {
         cand = {64, 128, 256};
     }

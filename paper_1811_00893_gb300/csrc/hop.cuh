@@ -387,4 +387,54 @@ __device__ __forceinline__ void stage_links(char* sm, const char* gl, long long 
 }
 
 
+// Asynchronous variant (cp.async, sm_80+): the copies of the tile are issued
+// without waiting; the caller commits them as one group and waits for the
+// group before reading the tile.  Lets a block fetch the next tile's links
+// while it computes on the current one.
+__device__ __forceinline__ void cp_async16(void* sm, const void* gl)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(sm);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gl) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sm, const void* gl)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(sm);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(a), "l"(gl) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sm, const void* gl)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(sm);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(gl) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N committed groups of this thread are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int P>
+__device__ __forceinline__ void stage_links_async(char* sm, const char* gl, long long Vh, int base, int n)
+{
+    using LP = LinkPlanes<P>;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    for (int e = tid; e < LP::n16 * kTile; e += nt) {
+        const int q = e / kTile, j = e - q * kTile;
+        if (j < n) cp_async16((uint4*)sm + q * kTile + j, (const uint4*)gl + q * Vh + base + j);
+    }
+    if (LP::nsmall) {
+        const char* gs = gl + (size_t)LP::n16 * 16 * Vh;
+        char* ss = sm + LP::n16 * 16 * kTile;
+        for (int e = tid; e < LP::nsmall * kTile; e += nt) {
+            const int q = e / kTile, j = e - q * kTile;
+            if (j >= n) continue;
+            if (LP::small_bytes == 8)
+                cp_async8((uint2*)ss + q * kTile + j, (const uint2*)gs + q * Vh + base + j);
+            else
+                cp_async4((unsigned*)ss + q * kTile + j, (const unsigned*)gs + q * Vh + base + j);
+        }
+    }
+}
+
 }  // namespace wl

@@ -1,7 +1,8 @@
 // The hopping kernels of Eq. 1 (and, through the epilogue's clover modes, of
 // Eq. 2), as templates over precision P, dagger DAG, fused reduction DOT and
-// clover mode CL.  dslash.cu instantiates the Wilson kernels (CL = 0) and
-// dslash_clover.cu the clover ones, so the two compile in parallel.
+// clover mode CL.  dslash.cu instantiates the Wilson kernels (CL = 0),
+// dslash_clover_x2.cu and dslash_clover_out.cu the clover ones, so the three
+// compile in parallel.
 //
 // One thread per output site of one parity.  The eight neighbour spinors are
 // spin-projected to half spinors (12 reals), multiplied by the link (folded
@@ -137,6 +138,83 @@ __global__ void __launch_bounds__(256, (MinBlocks<P, DOT>::value)) hop_mrhs_kern
     }
 }
 
+// Persistent, software-pipelined form of hop_mrhs_kernel for the narrow
+// types: a grid of resident blocks walks the 32-site tiles round-robin
+// (tile = blockIdx.x + k * gridDim.x, a fixed assignment, so the reduction
+// order is deterministic); while its warps compute on one tile's links the
+// block already copies the next tile's links into the other half of a
+// double buffer with cp.async.  Partial sums are written per tile, as in
+// hop_mrhs_kernel, and added up in tile order by the finishing launch.
+template <int P, bool DAG, bool DOT, int CL>
+__global__ void __launch_bounds__(256, 2) hop_mrhs_pipe_kernel(const HopArgs A, int nrhs, int ntiles)
+{
+    using T = typename Prec<P>::real;
+    extern __shared__ __align__(16) char smem[];
+    constexpr int kBuf = (int)Prec<P>::link_bytes * kTile;
+    double* bpart = (double*)(smem + 2 * kBuf);
+    const int lane = threadIdx.x;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    auto tile_at = [&](int t, int& pidx, int& base, int& n) {
+        pidx = t / A.blocks_per_parity;
+        base = (t - pidx * A.blocks_per_parity) * kTile;
+        n = (int)min((long long)kTile, A.g.Vh - base);
+    };
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    {
+        int pidx, base, n;
+        tile_at(tile, pidx, base, n);
+        stage_links_async<P>(smem, (const char*)A.links[pidx], A.g.Vh, base, n);
+        cp_async_commit();
+    }
+    for (int it = 0; tile < ntiles; ++it) {
+        const int next = tile + gridDim.x;
+        if (next < ntiles) {  // prefetch the next tile into the other buffer
+            int pidx, base, n;
+            tile_at(next, pidx, base, n);
+            stage_links_async<P>(smem + ((it + 1) & 1) * kBuf, (const char*)A.links[pidx], A.g.Vh,
+                                 base, n);
+        }
+        cp_async_commit();  // (an empty group on the last tile)
+        cp_async_wait<1>();  // this tile's copies have landed
+        __syncthreads();
+        const char* links = smem + (it & 1) * kBuf;
+        int pidx, base, n;
+        tile_at(tile, pidx, base, n);
+        const int p = A.parity0 + pidx;
+        const int i = base + lane;
+        const bool valid = lane < n;
+        int nb[8];
+        if (valid) neighbours(A.g, p, i, nb);
+        for (int r = threadIdx.y; r < nrhs; r += blockDim.y) {
+            const bool act = !A.active || A.active[r * A.active_stride] != 0;  // warp-uniform
+            T part[3] = {0, 0, 0};
+            if (act && valid) {
+                cx<T> acc[12];
+                hop_site<P, DAG>(acc, nb, A.g.Vh, A.in[pidx] + r * A.rs_in, links, kTile, lane);
+                epilogue<P, DOT, CL>(acc, A, pidx, r, i, part);
+            }
+            if (DOT) {
+                typename RedType<T>::type rp[3] = {(typename RedType<T>::type)part[0],
+                                                   (typename RedType<T>::type)part[1],
+                                                   (typename RedType<T>::type)part[2]};
+                warp_sum<3>(rp);
+                if (lane == 0)
+                    for (int k = 0; k < 3; ++k) bpart[3 * r + k] = (double)rp[k];
+            }
+        }
+        if (DOT) {
+            __syncthreads();
+            for (int e = tid; e < 3 * nrhs; e += nt) {
+                const int r = e / 3, k = e - 3 * r;
+                A.red.partial[((long long)r * A.red.max_blocks + tile) * 3 + k] = bpart[e];
+            }
+        }
+        __syncthreads();  // the buffer and bpart are reused by the tile after next
+        tile = next;
+    }
+}
+
 // Host-side launchers of one clover mode.
 template <int CL>
 struct HopKernels {
@@ -144,6 +222,10 @@ struct HopKernels {
                        cudaStream_t s);
     static void multi(int prec, bool dagger, bool dot, const HopArgs& A, int nrhs, dim3 grid,
                       dim3 block, size_t smem, cudaStream_t s);
+    // pipelined multi-RHS kernel (FP32 / FP16 only)
+    static void pipe(int prec, bool dagger, bool dot, const HopArgs& A, int nrhs, int ntiles, dim3 grid,
+                     dim3 block, size_t smem, cudaStream_t s);
+    static const void* pipe_kernel(int prec, bool dagger, bool dot);
     // the reducing single-RHS kernel (for occupancy queries)
     static const void* reducing(int prec, bool dagger);
 };
@@ -171,6 +253,43 @@ static void hop_multi_p(bool dagger, bool dot, const HopArgs& A, int nrhs, dim3 
         if (dot) hop_mrhs_kernel<P, false, true, CL><<<grid, block, smem, s>>>(A, nrhs);
         else hop_mrhs_kernel<P, false, false, CL><<<grid, block, smem, s>>>(A, nrhs);
     }
+}
+
+template <int CL, int P>
+static void hop_pipe_p(bool dagger, bool dot, const HopArgs& A, int nrhs, int ntiles, dim3 grid,
+                       dim3 block, size_t smem, cudaStream_t s)
+{
+    if (dagger) {
+        if (dot) hop_mrhs_pipe_kernel<P, true, true, CL><<<grid, block, smem, s>>>(A, nrhs, ntiles);
+        else hop_mrhs_pipe_kernel<P, true, false, CL><<<grid, block, smem, s>>>(A, nrhs, ntiles);
+    } else {
+        if (dot) hop_mrhs_pipe_kernel<P, false, true, CL><<<grid, block, smem, s>>>(A, nrhs, ntiles);
+        else hop_mrhs_pipe_kernel<P, false, false, CL><<<grid, block, smem, s>>>(A, nrhs, ntiles);
+    }
+}
+
+template <int CL, int P>
+static const void* pipe_kernel_p(bool dagger, bool dot)
+{
+    if (dagger)
+        return dot ? (const void*)hop_mrhs_pipe_kernel<P, true, true, CL>
+                   : (const void*)hop_mrhs_pipe_kernel<P, true, false, CL>;
+    return dot ? (const void*)hop_mrhs_pipe_kernel<P, false, true, CL>
+               : (const void*)hop_mrhs_pipe_kernel<P, false, false, CL>;
+}
+
+template <int CL>
+void HopKernels<CL>::pipe(int prec, bool dagger, bool dot, const HopArgs& A, int nrhs, int ntiles,
+                          dim3 grid, dim3 block, size_t smem, cudaStream_t s)
+{
+    if (prec == WL_F32) hop_pipe_p<CL, WL_F32>(dagger, dot, A, nrhs, ntiles, grid, block, smem, s);
+    else hop_pipe_p<CL, WL_F16>(dagger, dot, A, nrhs, ntiles, grid, block, smem, s);
+}
+
+template <int CL>
+const void* HopKernels<CL>::pipe_kernel(int prec, bool dagger, bool dot)
+{
+    return prec == WL_F32 ? pipe_kernel_p<CL, WL_F32>(dagger, dot) : pipe_kernel_p<CL, WL_F16>(dagger, dot);
 }
 
 template <int CL>
