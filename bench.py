@@ -61,6 +61,8 @@ def parse_args(argv=None):
                     help="target duration of the oracle sample")
     ap.add_argument("--workload", type=int, default=WORKLOAD_INDEX,
                     help="workload index (workloads.WORKLOADS); the default is the headline one")
+    ap.add_argument("--no-r12", action="store_true",
+                    help="skip the compressed-link measurement")
     ap.add_argument("--dims", type=str, default=None,
                     help="override the lattice extents, e.g. 24,24,24,48 (smaller profiling runs)")
     return ap.parse_args(argv)
@@ -312,11 +314,16 @@ def run_ours(args, rank, world, local):
     U_host = U.cpu().numpy() if want_cpu else None
     b_host = b[0].cpu().numpy() if want_cpu else None
     g = wilson.Gauge(wl.dims, wl.kappa, U, precs=("f64", pname), bc=wl.bc)
+    # the same operator with compressed (two-row) links, measured beside it
+    g12 = (wilson.Gauge(wl.dims, wl.kappa, U, precs=("f64", pname), bc=wl.bc, r12=True)
+           if pname in ("f32", "f16") and not args.no_r12 else None)
     del U
     F_host = None
     if wl.clover:  # D_clov of Eq. 2: attach the seeded synthetic clover field
         F = fields.clover_field(wl.dims, wl.clover_seed, device=dev)
         wilson.wl_clover_set(g.handle, F)
+        if g12 is not None:
+            wilson.wl_clover_set(g12.handle, F)
         F_host = F.cpu().numpy() if want_cpu else None
         del F
     torch.cuda.empty_cache()
@@ -411,6 +418,37 @@ def run_ours(args, rank, world, local):
                                 "bytes_per_site": mbps, "frac_hbm": mbps * Vh / mult_s / 1e9 / peak,
                                 "launches_per_apply": 2}
 
+    # ---------------- compressed links: the same Dslash protocol and solve
+    r12 = None
+    if g12 is not None:
+        for _ in range(10):
+            wilson.wilson_dslash(g12.handle, fout, fin, 0, 0, P, nr)
+        torch.cuda.synchronize()
+        d0.record(stream)
+        for _ in range(1000):
+            wilson.wilson_dslash(g12.handle, fout, fin, 0, 0, P, nr)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        r12_s = d0.elapsed_time(d1) / 1e3 / 1000
+        cb = costs.hop_bytes_per_site(pname, nrhs=nr, r12=True)
+        x12 = torch.zeros_like(b)
+        rc12, inf12 = wilson.wilson_solve(g12.handle, x12, b, wl.nrhs, mixed)  # warm
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(3):
+            rc12, inf12 = wilson.wilson_solve(g12.handle, x12, b, wl.nrhs, mixed)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        r12 = {"dslash_us_per_launch": r12_s * 1e6,
+               "dslash_gbs_compressed_bytes": cb * Vh / r12_s / 1e9,
+               "dslash_gbs_equivalent": bps * Vh / r12_s / 1e9,
+               "dslash_gflops": costs.FLOPS_HOP_SITE * Vh * nr / r12_s / 1e9,
+               "bytes_per_site_compressed": cb,
+               "solve_ms": f0.elapsed_time(f1) / 3, "solve_iters": max(i["iters"] for i in inf12),
+               "solve_true_resid": max(i["true_resid"] for i in inf12)}
+        g12.close()
+
     # ---------------- plain FP64 GPU solve for the time-to-solution comparison
     x64 = torch.zeros_like(b)
     p64 = wilson.solve_params(tol=1e-10, eo=wl.eo, inner=wilson.WL_F64, graph_iters=0)
@@ -471,6 +509,7 @@ def run_ours(args, rank, world, local):
             "launch_index_range": [l0, l0 + launches],
             "roofline": roofline,
             "dslash": dslash,
+            "r12": r12,
             "solve": {"mixed_ms": ms_per_step, "fp64_ms": fp64_ms,
                       "speedup_vs_fp64": fp64_ms / ms_per_step,
                       "mixed_iters": max(i["iters"] for i in infos[-nr:]),

@@ -59,6 +59,16 @@ typedef enum { WL_F64 = 0, WL_F32 = 1, WL_F16 = 2, WL_DF64 = 3 } wl_prec;
 #define WL_PREC_MASK(p) (1 << (p))
 #define WL_PREC_ALL 15
 
+/* Flag for wl_gauge_create's prec_mask: also keep the FP32 / FP16 links in a
+ * compressed form -- the first two rows of each SU(3) matrix, the third
+ * rebuilt in the kernel as the complex conjugate of their cross product, the
+ * boundary phase applied on the fly -- and use it in the hopping kernels of
+ * those precisions: 384 instead of 576 bytes of links per site in FP32 (192
+ * instead of 288 in FP16), a bandwidth reduction of the Table 1 traffic.
+ * Requires SU(3) links (unitary with det 1 to 1e-6; checked, WL_ERR_ARG
+ * otherwise).  The uneven-batch solver keeps using the full links. */
+#define WL_LINKS_R12 (1 << 8)
+
 enum {
     WL_OK = 0,
     WL_ERR_ARG = -1,            /* invalid argument (message says which) */

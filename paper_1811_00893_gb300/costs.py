@@ -54,8 +54,10 @@ def spinor_bytes(prec: str) -> int:
     return SPINOR_REALS * WORD[prec] + NORM_BYTES[prec]
 
 
-def link_bytes(prec: str) -> int:
-    return LINK_REALS * WORD[prec]
+def link_bytes(prec: str, r12: bool = False) -> int:
+    """Bytes of one stored link: 18 reals, or 12 with two-row compression
+    (the third row rebuilt from unitarity)."""
+    return (12 if r12 else LINK_REALS) * WORD[prec]
 
 
 #: reals of the clover term per site (Eq. 2): two Hermitian 6x6 blocks = 2 x 36
@@ -69,13 +71,13 @@ def clover_bytes(prec: str) -> int:
 
 
 def hop_bytes_per_site(prec: str, nrhs: int = 1, extra_in: int = 0, extra_out: int = 0,
-                       clover: bool = False) -> int:
+                       clover: bool = False, r12: bool = False) -> int:
     """Algorithmic bytes per output site of one even-odd hopping kernel:
     eight links (and, with the clover term fused, one clover matrix) read
     once for all right-hand sides, one input spinor and one output spinor per
     right-hand side, plus `extra_in` / `extra_out` fused epilogue fields per
     right-hand side."""
-    return (8 * link_bytes(prec) + (clover_bytes(prec) if clover else 0) +
+    return (8 * link_bytes(prec, r12) + (clover_bytes(prec) if clover else 0) +
             nrhs * (1 + extra_in + 1 + extra_out) * spinor_bytes(prec))
 
 

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) batch_hop_kernel(const BatchArgs B)
     constexpr int par = DOT ? 0 : 1;  // output parity
     extern __shared__ __align__(16) char smem[];
     double* bpart = (double*)(smem + Prec<P>::link_bytes * kTile);
-    __shared__ int s_item, s_lat;
+    __shared__ int s_item, s_lat, s_any;
     __shared__ bool last;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
     const int lane = threadIdx.x;
@@ -78,10 +78,20 @@ __global__ void __launch_bounds__(256) batch_hop_kernel(const BatchArgs B)
             }
             s_item = it;
             s_lat = lo;
+            // a lattice whose systems are all inactive (converged, or between
+            // rounds) needs neither its links nor any arithmetic
+            int any = 0;
+            if (it < B.total_items)
+                for (int r = 0; r < B.lats[lo].nrhs && !any; ++r) any = B.lats[lo].sc[r].active != 0;
+            s_any = any;
         }
         __syncthreads();
         const int item = s_item;
         if (item >= B.total_items) break;
+        if (!s_any) {  // (its partial sums are never read: the finishing launch skips inactive systems)
+            __syncthreads();
+            continue;
+        }
         const BLat& L = B.lats[s_lat];
         const int base = (item - L.item0) * kTile;
         const int n = (int)min((long long)kTile, L.g.Vh - base);

@@ -14,9 +14,40 @@
 
 namespace wl {
 
-// the clover variants are instantiated in dslash_clover_x2.cu and dslash_clover_out.cu
-extern template struct HopKernels<kClX2>;
-extern template struct HopKernels<kClOut>;
+// the other variants are instantiated in their own translation units:
+// clover modes in dslash_clover_x2.cu / dslash_clover_out.cu, compressed links
+// (LF = 1) in dslash_r12.cu / dslash_r12_clover.cu
+extern template struct HopKernels<kClX2, 0>;
+extern template struct HopKernels<kClOut, 0>;
+extern template struct HopKernels<kClNone, 1>;
+extern template struct HopKernels<kClX2, 1>;
+extern template struct HopKernels<kClOut, 1>;
+
+// The kernel family of a launch: clover mode and link format.
+template <typename F>
+static void with_variant(const HopLaunch& h, int lf, F&& f)
+{
+    if (lf) {
+        switch (h.cl_mode) {
+            case kClX2: f(HopKernels<kClX2, 1>()); break;
+            case kClOut: f(HopKernels<kClOut, 1>()); break;
+            default: f(HopKernels<kClNone, 1>()); break;
+        }
+    } else {
+        switch (h.cl_mode) {
+            case kClX2: f(HopKernels<kClX2, 0>()); break;
+            case kClOut: f(HopKernels<kClOut, 0>()); break;
+            default: f(HopKernels<kClNone, 0>()); break;
+        }
+    }
+}
+
+// Bytes of the links of one site (all eight hops) in the launch's format.
+static size_t link_site_bytes(int prec, int lf)
+{
+    if (lf) return prec == WL_F32 ? 384 : 192;
+    return link_field_bytes(prec, 1);
+}
 
 // ---------------------------------------------------------------------------
 // host side
@@ -24,40 +55,29 @@ extern template struct HopKernels<kClOut>;
 
 static const int kHopBlock = 128;
 
-static void launch_single(const HopLaunch& h, const HopArgs& A, dim3 grid, int block, cudaStream_t s)
+static void launch_single(const HopLaunch& h, int lf, const HopArgs& A, dim3 grid, int block,
+                          cudaStream_t s)
 {
-    switch (h.cl_mode) {
-        case kClX2: HopKernels<kClX2>::single(h.prec, h.dagger, h.dot, A, grid, block, s); break;
-        case kClOut: HopKernels<kClOut>::single(h.prec, h.dagger, h.dot, A, grid, block, s); break;
-        default: HopKernels<kClNone>::single(h.prec, h.dagger, h.dot, A, grid, block, s); break;
-    }
+    with_variant(h, lf, [&](auto K) { K.single(h.prec, h.dagger, h.dot, A, grid, block, s); });
 }
 
-static void launch_multi(const HopLaunch& h, const HopArgs& A, int nrhs, dim3 grid, dim3 block,
+static void launch_multi(const HopLaunch& h, int lf, const HopArgs& A, int nrhs, dim3 grid, dim3 block,
                          size_t smem, cudaStream_t s)
 {
-    switch (h.cl_mode) {
-        case kClX2: HopKernels<kClX2>::multi(h.prec, h.dagger, h.dot, A, nrhs, grid, block, smem, s); break;
-        case kClOut: HopKernels<kClOut>::multi(h.prec, h.dagger, h.dot, A, nrhs, grid, block, smem, s); break;
-        default: HopKernels<kClNone>::multi(h.prec, h.dagger, h.dot, A, nrhs, grid, block, smem, s); break;
-    }
+    with_variant(h, lf, [&](auto K) { K.multi(h.prec, h.dagger, h.dot, A, nrhs, grid, block, smem, s); });
 }
 
-static void launch_pipe(const HopLaunch& h, const HopArgs& A, int nrhs, int ntiles, dim3 grid,
+static void launch_pipe(const HopLaunch& h, int lf, const HopArgs& A, int nrhs, int ntiles, dim3 grid,
                         dim3 block, size_t smem, cudaStream_t s)
 {
-    switch (h.cl_mode) {
-        case kClX2: HopKernels<kClX2>::pipe(h.prec, h.dagger, h.dot, A, nrhs, ntiles, grid, block, smem, s); break;
-        case kClOut: HopKernels<kClOut>::pipe(h.prec, h.dagger, h.dot, A, nrhs, ntiles, grid, block, smem, s); break;
-        default: HopKernels<kClNone>::pipe(h.prec, h.dagger, h.dot, A, nrhs, ntiles, grid, block, smem, s); break;
-    }
+    with_variant(h, lf, [&](auto K) { K.pipe(h.prec, h.dagger, h.dot, A, nrhs, ntiles, grid, block, smem, s); });
 }
 
-static const void* pipe_kernel(const HopLaunch& h)
+static const void* pipe_kernel(const HopLaunch& h, int lf)
 {
-    return h.cl_mode == kClX2    ? HopKernels<kClX2>::pipe_kernel(h.prec, h.dagger, h.dot)
-           : h.cl_mode == kClOut ? HopKernels<kClOut>::pipe_kernel(h.prec, h.dagger, h.dot)
-                                 : HopKernels<kClNone>::pipe_kernel(h.prec, h.dagger, h.dot);
+    const void* k = nullptr;
+    with_variant(h, lf, [&](auto K) { k = K.pipe_kernel(h.prec, h.dagger, h.dot); });
+    return k;
 }
 
 // Multi-RHS launch shapes: 1..8 = right-hand-side lanes (warps) of
@@ -65,18 +85,17 @@ static const void* pipe_kernel(const HopLaunch& h)
 static const int kPipeShape = 16;
 
 // Resident-block grid of the reducing single-RHS hop kernel.
-static int single_grid_cap(const HopLaunch& h, int block)
+static int single_grid_cap(const HopLaunch& h, int lf, int block)
 {
-    const void* k = h.cl_mode == kClX2    ? HopKernels<kClX2>::reducing(h.prec, h.dagger)
-                    : h.cl_mode == kClOut ? HopKernels<kClOut>::reducing(h.prec, h.dagger)
-                                          : HopKernels<kClNone>::reducing(h.prec, h.dagger);
+    const void* k = nullptr;
+    with_variant(h, lf, [&](auto K) { k = K.reducing(h.prec, h.dagger); });
     return resident_grid(k, block, 0);
 }
 
 // Launch one chunk of right-hand sides with launch shape `shape`: threads per
 // block for the single-RHS kernel, right-hand-side lanes (warps) per block for
 // the multi-RHS kernel.
-static int launch_shape(const HopLaunch& h, HopArgs& A, int nrhs, int shape, cudaStream_t s)
+static int launch_shape(const HopLaunch& h, int lf, HopArgs& A, int nrhs, int shape, cudaStream_t s)
 {
     const bool multi = nrhs > 1;
     const int tile = multi ? kTile : shape;
@@ -85,21 +104,21 @@ static int launch_shape(const HopLaunch& h, HopArgs& A, int nrhs, int shape, cud
     A.nparity = h.nparity;
     unsigned gx = (unsigned)(bpp * h.nparity);
     if (!multi) {
-        if (h.dot) gx = std::min(gx, (unsigned)single_grid_cap(h, shape));
-        launch_single(h, A, dim3(gx, 1), shape, s);
+        if (h.dot) gx = std::min(gx, (unsigned)single_grid_cap(h, lf, shape));
+        launch_single(h, lf, A, dim3(gx, 1), shape, s);
     } else if (shape > kPipeShape) {
         const dim3 block(kTile, shape - kPipeShape);
-        const size_t smem = 2 * link_field_bytes(h.prec, kTile) + sizeof(double) * 3 * nrhs;
+        const size_t smem = 2 * link_site_bytes(h.prec, lf) * kTile + sizeof(double) * 3 * nrhs;
         const int ntiles = (int)gx;
-        const int grid = std::min(ntiles, resident_grid(pipe_kernel(h), kTile * (shape - kPipeShape), smem));
-        launch_pipe(h, A, nrhs, ntiles, dim3((unsigned)grid), block, smem, s);
+        const int grid = std::min(ntiles, resident_grid(pipe_kernel(h, lf), kTile * (shape - kPipeShape), smem));
+        launch_pipe(h, lf, A, nrhs, ntiles, dim3((unsigned)grid), block, smem, s);
         if (h.dot)  // per-tile partials, added in tile order
             return launch_finish_slots(A.red.partial, (long long)A.red.max_blocks * 3, ntiles, nrhs,
                                        A.dot_out, A.dot_stride, A.active, A.active_stride, s);
     } else {
         const dim3 block(kTile, shape);
-        const size_t smem = link_field_bytes(h.prec, kTile) + sizeof(double) * 3 * nrhs;
-        launch_multi(h, A, nrhs, dim3(gx), block, smem, s);
+        const size_t smem = link_site_bytes(h.prec, lf) * kTile + sizeof(double) * 3 * nrhs;
+        launch_multi(h, lf, A, nrhs, dim3(gx), block, smem, s);
         if (h.dot)  // add the per-block partials of each right-hand side
             return launch_finish_slots(A.red.partial, (long long)A.red.max_blocks * 3, (int)gx, nrhs,
                                        A.dot_out, A.dot_stride, A.active, A.active_stride, s);
@@ -120,14 +139,14 @@ static bool autotune_enabled()
 // (first use, outside stream capture) the fastest candidate timed with CUDA
 // events on the launching stream.  Re-running a hopping launch is harmless:
 // it is out of place and its reductions are recomputed from scratch.
-static int tuned_shape(wl_gauge g, const HopLaunch& h, HopArgs& A, int nrhs, cudaStream_t s,
+static int tuned_shape(wl_gauge g, const HopLaunch& h, int lf, HopArgs& A, int nrhs, cudaStream_t s,
                        int* shape)
 {
     const bool multi = nrhs > 1;
     const int dflt = multi ? (nrhs < 8 ? nrhs : 8) : kHopBlock;
     char key[96];
-    snprintf(key, sizeof key, "hop p%d d%d dot%d np%d r%d x%d%d w%d c%d", h.prec, h.dagger, (int)h.dot,
-             h.nparity, nrhs, h.x1[0] != nullptr, h.x2[0] != nullptr, h.w[0] != nullptr, h.cl_mode);
+    snprintf(key, sizeof key, "hop p%d d%d dot%d np%d r%d x%d%d w%d c%d l%d", h.prec, h.dagger, (int)h.dot,
+             h.nparity, nrhs, h.x1[0] != nullptr, h.x2[0] != nullptr, h.w[0] != nullptr, h.cl_mode, lf);
     auto it = g->tuned.find(key);
     if (it != g->tuned.end()) {
         *shape = it->second.block;
@@ -166,7 +185,7 @@ static int tuned_shape(wl_gauge g, const HopLaunch& h, HopArgs& A, int nrhs, cud
     WL_CUDA(cudaEventCreate(&e0));
     WL_CUDA(cudaEventCreate(&e1));
     for (int c : cand) {  // warm every candidate once
-        WL_TRY(launch_shape(h, A, nrhs, c, s));
+        WL_TRY(launch_shape(h, lf, A, nrhs, c, s));
         WL_CHECK_LAUNCH(0.0);
     }
     // interleaved rounds so that a drifting clock or cache state affects every
@@ -175,7 +194,7 @@ static int tuned_shape(wl_gauge g, const HopLaunch& h, HopArgs& A, int nrhs, cud
     for (int round = 0; round < 4; ++round)
         for (size_t ci = 0; ci < cand.size(); ++ci) {
             cudaEventRecord(e0, s);
-            WL_TRY(launch_shape(h, A, nrhs, cand[ci], s));
+            WL_TRY(launch_shape(h, lf, A, nrhs, cand[ci], s));
             cudaEventRecord(e1, s);
             WL_CHECK_LAUNCH(0.0);
             WL_CUDA(cudaEventSynchronize(e1));
@@ -201,7 +220,7 @@ static int tuned_shape(wl_gauge g, const HopLaunch& h, HopArgs& A, int nrhs, cud
     return WL_OK;
 }
 
-static int launch_hop_chunk(wl_gauge g, const HopLaunch& h, HopArgs A, int nrhs, cudaStream_t s)
+static int launch_hop_chunk(wl_gauge g, const HopLaunch& h, int lf, HopArgs A, int nrhs, cudaStream_t s)
 {
     const bool multi = nrhs > 1;
     if (h.dot) {  // sized for the smallest tile any candidate shape uses
@@ -210,17 +229,17 @@ static int launch_hop_chunk(wl_gauge g, const HopLaunch& h, HopArgs A, int nrhs,
     }
     A.red = g->red;
     int shape = 0;
-    WL_TRY(tuned_shape(g, h, A, nrhs, s, &shape));
+    WL_TRY(tuned_shape(g, h, lf, A, nrhs, s, &shape));
     (void)multi;
     // algorithmic bytes: links once for all rhs; in, out and epilogue fields per rhs
     // (and the clover matrix once, like the links)
     const int extra = (h.x1[0] ? 1 : 0) + (h.x2[0] ? 1 : 0) + (h.w[0] ? 1 : 0);
     const double bytes = (double)g->geo.Vh * h.nparity *
-                         (link_field_bytes(h.prec, 1) + (h.cl_mode ? clover_site_bytes(h.prec) : 0) +
+                         (link_site_bytes(h.prec, lf) + (h.cl_mode ? clover_site_bytes(h.prec) : 0) +
                           (double)nrhs * (2 + extra) * spinor_field_bytes(h.prec, 1));
     int slot = -1;
     timing_begin(g, s, bytes, h.prec, &slot);
-    WL_TRY(launch_shape(h, A, nrhs, shape, s));
+    WL_TRY(launch_shape(h, lf, A, nrhs, shape, s));
     WL_CHECK_LAUNCH(bytes);
     timing_end(g, s, slot);
     return WL_OK;
@@ -230,13 +249,18 @@ int launch_hop(wl_gauge g, const HopLaunch& h, cudaStream_t s)
 {
     if (!g->links[h.prec][0])
         return set_error(WL_ERR_STATE, "gauge object has no links in the requested precision");
+    // compressed links when the gauge object holds them (WL_NO_R12 turns them
+    // off, for comparisons)
+    static const bool r12_off = getenv("WL_NO_R12") != nullptr;
+    const int lf = (h.prec == WL_F32 || h.prec == WL_F16) && g->links_r12[h.prec][0] && !r12_off ? 1 : 0;
     HopArgs A;
     A.g = g->geo;
     for (int k = 0; k < 2; ++k) {
         const int p = h.parity0 + (k < h.nparity ? k : 0);
-        A.links[k] = g->links[h.prec][p];
+        A.links[k] = lf ? g->links_r12[h.prec][p] : g->links[h.prec][p];
         A.cl[k] = h.clov[k];
     }
+    for (int mu = 0; mu < 4; ++mu) A.ph[mu] = {(float)g->bc_re[mu], (float)g->bc_im[mu]};
     if (h.cl_mode && (!h.clov[0] || (h.nparity == 2 && !h.clov[1])))
         return set_error(WL_ERR_STATE, "gauge object has no clover term in the requested precision");
     A.rs_in = h.rs_in;
@@ -264,7 +288,7 @@ int launch_hop(wl_gauge g, const HopLaunch& h, cudaStream_t s)
         }
         A.dot_out = h.dot_out ? h.dot_out + (long long)r0 * h.dot_stride : nullptr;
         A.active = h.active ? h.active + (long long)r0 * h.active_stride : nullptr;
-        WL_TRY(launch_hop_chunk(g, h, A, n, s));
+        WL_TRY(launch_hop_chunk(g, h, lf, A, n, s));
     }
     return WL_OK;
 }

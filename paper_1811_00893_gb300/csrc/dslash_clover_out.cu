@@ -6,6 +6,6 @@
 
 namespace wl {
 
-template struct HopKernels<kClOut>;
+template struct HopKernels<kClOut, 0>;
 
 }  // namespace wl

@@ -7,6 +7,6 @@
 
 namespace wl {
 
-template struct HopKernels<kClX2>;
+template struct HopKernels<kClX2, 0>;
 
 }  // namespace wl

@@ -137,6 +137,83 @@ __global__ void build_links_kernel(void* out, const double* __restrict__ U, Geom
     }
 }
 
+// Compressed links (LF = 1 of the hopping kernels): rows 0 and 1 of the
+// hop matrices U_mu(x) and U_mu(x - mu)^dag without the boundary phase; the
+// kernels rebuild row 2 from unitarity.  Set-up checks that every link is in
+// SU(3) to 1e-6 (max |U U^dag - 1| and |det U - 1|) and raises *flag if not.
+template <int P>
+__device__ __forceinline__ void store_link_r12(void* base, long long Vh, int d, long long i,
+                                               const cx<double> (&w)[9]);
+template <>
+__device__ __forceinline__ void store_link_r12<WL_F32>(void* base, long long Vh, int d, long long i,
+                                                       const cx<double> (&w)[9])
+{
+    float4* p = (float4*)base + (long long)d * 3 * Vh;
+    for (int k = 0; k < 3; ++k)
+        p[k * Vh + i] = make_float4((float)w[2 * k].re, (float)w[2 * k].im, (float)w[2 * k + 1].re,
+                                    (float)w[2 * k + 1].im);
+}
+template <>
+__device__ __forceinline__ void store_link_r12<WL_F16>(void* base, long long Vh, int d, long long i,
+                                                       const cx<double> (&w)[9])
+{
+    uint4 t;
+    t.x = f2h((float)w[0].re, (float)w[0].im);
+    t.y = f2h((float)w[1].re, (float)w[1].im);
+    t.z = f2h((float)w[2].re, (float)w[2].im);
+    t.w = f2h((float)w[3].re, (float)w[3].im);
+    ((uint4*)base)[(long long)d * Vh + i] = t;
+    uint2 u;
+    u.x = f2h((float)w[4].re, (float)w[4].im);
+    u.y = f2h((float)w[5].re, (float)w[5].im);
+    ((uint2*)((uint4*)base + 8 * Vh))[(long long)d * Vh + i] = u;
+}
+
+// max |U U^dag - 1| and |det U - 1| of a 3x3 complex matrix
+__device__ double su3_deviation(const double* u)
+{
+    auto at = [&](int a, int b) { return cx<double>{u[2 * (3 * a + b)], u[2 * (3 * a + b) + 1]}; };
+    double dev = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            cx<double> sum = {a == b ? -1.0 : 0.0, 0.0};
+            for (int k = 0; k < 3; ++k) sum = sum + at(a, k) * conj(at(b, k));
+            dev = fmax(dev, hypot(sum.re, sum.im));
+        }
+    const cx<double> det = at(0, 0) * (at(1, 1) * at(2, 2) - at(1, 2) * at(2, 1)) -
+                           at(0, 1) * (at(1, 0) * at(2, 2) - at(1, 2) * at(2, 0)) +
+                           at(0, 2) * (at(1, 0) * at(2, 1) - at(1, 1) * at(2, 0));
+    return fmax(dev, hypot(det.re - 1.0, det.im));
+}
+
+template <int P>
+__global__ void build_links_r12_kernel(void* out, const double* __restrict__ U, Geom g, int p, int* flag)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.Vh) return;
+    const long long s = site_of_half(g, p, i);
+    int c[4];
+    long long r = s;
+    for (int mu = 0; mu < 4; ++mu) {
+        c[mu] = (int)(r % g.L[mu]);
+        r /= g.L[mu];
+    }
+    const long long stride[4] = {1, g.L[0], (long long)g.L[0] * g.L[1],
+                                 (long long)g.L[0] * g.L[1] * g.L[2]};
+    for (int mu = 0; mu < 4; ++mu) {
+        cx<double> w[9];
+        const double* u = U + (s * 4 + mu) * 18;
+        if (su3_deviation(u) > 1e-6) atomicOr(flag, 1);
+        for (int k = 0; k < 9; ++k) w[k] = {u[2 * k], u[2 * k + 1]};
+        store_link_r12<P>(out, g.Vh, 2 * mu, i, w);
+        const long long n = (c[mu] == 0) ? s + (g.L[mu] - 1) * stride[mu] : s - stride[mu];
+        const double* v = U + (n * 4 + mu) * 18;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) w[a * 3 + b] = {v[2 * (b * 3 + a)], -v[2 * (b * 3 + a) + 1]};
+        store_link_r12<P>(out, g.Vh, 2 * mu + 1, i, w);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // fermion layout conversion
 // ---------------------------------------------------------------------------
@@ -313,6 +390,39 @@ extern "C" int wl_gauge_create(wl_gauge* out, const wl_lattice* lat, const doubl
             }
         }
         if (rc != WL_OK) break;
+        if (prec_mask & WL_LINKS_R12) {  // compressed FP32 / FP16 copies
+            int* flag = nullptr;
+            if (cudaMalloc((void**)&flag, sizeof(int)) != cudaSuccess ||
+                cudaMemsetAsync(flag, 0, sizeof(int), s) != cudaSuccess) {
+                cudaGetLastError();
+                if (flag) cudaFree(flag);
+                rc = set_error(WL_ERR_CUDA, "cudaMalloc for the SU(3) check");
+                break;
+            }
+            for (int prec : {(int)WL_F32, (int)WL_F16}) {
+                if (!(g->prec_mask & WL_PREC_MASK(prec)) || rc != WL_OK) continue;
+                for (int p = 0; p < 2 && rc == WL_OK; ++p) {
+                    const size_t bytes = (prec == WL_F32 ? 384 : 192) * (size_t)g->geo.Vh;
+                    if (cudaMalloc(&g->links_r12[prec][p], bytes) != cudaSuccess) {
+                        cudaGetLastError();
+                        rc = set_error(WL_ERR_CUDA, "cudaMalloc compressed links");
+                        break;
+                    }
+                    if (prec == WL_F32) build_links_r12_kernel<WL_F32><<<grid, block, 0, s>>>(g->links_r12[prec][p], U, g->geo, p, flag);
+                    else build_links_r12_kernel<WL_F16><<<grid, block, 0, s>>>(g->links_r12[prec][p], U, g->geo, p, flag);
+                    if (cudaGetLastError() != cudaSuccess) rc = set_error(WL_ERR_CUDA, "compressed link build launch");
+                    count_launch(1, (double)g->geo.Vh * (8 * 144.0 + bytes / g->geo.Vh));
+                }
+            }
+            int hflag = 0;
+            if (rc == WL_OK && (cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                                cudaStreamSynchronize(s) != cudaSuccess))
+                rc = set_error(WL_ERR_CUDA, "compressed link build failed");
+            cudaFree(flag);
+            if (rc == WL_OK && hflag)
+                rc = set_error(WL_ERR_ARG, "WL_LINKS_R12 needs SU(3) links (unitary, det 1, to 1e-6)");
+            if (rc != WL_OK) break;
+        }
         // the link build reads U: finish before returning so U may be freed
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(WL_ERR_CUDA, "link build failed"); break; }
     } while (0);
@@ -335,8 +445,10 @@ extern "C" int wl_gauge_destroy(wl_gauge g)
     free_workspace(g);
     free_clover(g);
     for (int prec = 0; prec < 4; ++prec) {
-        for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < 2; ++p) {
             if (g->links[prec][p]) cudaFree(g->links[prec][p]);
+            if (g->links_r12[prec][p]) cudaFree(g->links_r12[prec][p]);
+        }
         if (g->tmp[prec]) cudaFree(g->tmp[prec]);
     }
     if (g->red.partial) cudaFree(g->red.partial);

@@ -198,26 +198,189 @@ __device__ __forceinline__ void neighbours(const Geom& g, int p, int i, int (&nb
     nb[7] = (t == 0) ? i + (g.L[3] - 1) * st : i - st;
 }
 
-template <int P, int D, int MU, int S>
-__device__ __forceinline__ void hop_one(cx<typename Prec<P>::real> (&acc)[12], const void* in,
-                                        long long Vh, int nb, const void* links, long long lVh,
-                                        int li)
+// neighbours() plus a mask of the hops that cross the lattice boundary (bit
+// d set for hop d): forward hops leaving x_mu = L_mu - 1, backward hops
+// leaving x_mu = 0.  Used by the compressed-link kernels, whose stored links
+// carry no boundary phase.
+__device__ __forceinline__ void neighbours(const Geom& g, int p, int i, int (&nb)[8], unsigned& cross)
+{
+    neighbours(g, p, i, nb);
+    const int xh = i % g.Lxh;
+    int r = i / g.Lxh;
+    const int y = r % g.L[1];
+    r /= g.L[1];
+    const int z = r % g.L[2];
+    const int t = r / g.L[2];
+    const int x = 2 * xh + ((p + y + z + t) & 1);
+    const int c[4] = {x, y, z, t};
+    cross = 0;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        if (c[mu] == g.L[mu] - 1) cross |= 1u << (2 * mu);
+        if (c[mu] == 0) cross |= 1u << (2 * mu + 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Link storage formats of the hopping kernels.  LF = 0: all nine entries of
+// each hop matrix, boundary phase folded in.  LF = 1 (FP32 / FP16 only): the
+// first two rows of the SU(3) matrix without the phase; the third row is
+// rebuilt as conj(row0 x row1) (unitarity with det = 1), and the phase is
+// applied to the projected half spinor of boundary-crossing hops.  Twelve
+// reals instead of eighteen per hop: 384 instead of 576 bytes per site in
+// FP32 (192 instead of 288 in FP16).
+// ---------------------------------------------------------------------------
+
+template <int P, int LF>
+struct LinkLayout;  // 16-byte planes, then narrower planes; bytes per site
+template <>
+struct LinkLayout<WL_F64, 0> {
+    static constexpr int n16 = 72, nsmall = 0, small_bytes = 8, bytes = 1152;
+};
+template <>
+struct LinkLayout<WL_F32, 0> {
+    static constexpr int n16 = 32, nsmall = 8, small_bytes = 8, bytes = 576;
+};
+template <>
+struct LinkLayout<WL_DF64, 0> {
+    static constexpr int n16 = 72, nsmall = 0, small_bytes = 8, bytes = 1152;
+};
+template <>
+struct LinkLayout<WL_F16, 0> {
+    static constexpr int n16 = 16, nsmall = 8, small_bytes = 4, bytes = 288;
+};
+template <>
+struct LinkLayout<WL_F32, 1> {  // per hop: 3 float4 = rows 0 and 1
+    static constexpr int n16 = 24, nsmall = 0, small_bytes = 8, bytes = 384;
+};
+template <>
+struct LinkLayout<WL_F16, 1> {  // per hop: 1 uint4 (4 half2) + 1 uint2 (2 half2)
+    static constexpr int n16 = 8, nsmall = 8, small_bytes = 8, bytes = 192;
+};
+
+// row 2 = conj(row 0 x row 1)
+template <typename T>
+__device__ __forceinline__ void su3_third_row(cx<T> (&w)[9])
+{
+    w[6] = conj(w[1] * w[5] - w[2] * w[4]);
+    w[7] = conj(w[2] * w[3] - w[0] * w[5]);
+    w[8] = conj(w[0] * w[4] - w[1] * w[3]);
+}
+
+// Compressed link of hop d at index i of planes with stride Vh.
+template <int P>
+__device__ __forceinline__ void load_link_r12(cx<float> (&w)[9], const void* base, long long Vh, int d,
+                                              long long i);
+template <>
+__device__ __forceinline__ void load_link_r12<WL_F32>(cx<float> (&w)[9], const void* base, long long Vh,
+                                                      int d, long long i)
+{
+    const float4* p = (const float4*)base + (long long)d * 3 * Vh;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float4 t = p[k * Vh + i];
+        w[2 * k] = {t.x, t.y};
+        w[2 * k + 1] = {t.z, t.w};
+    }
+    su3_third_row(w);
+}
+template <>
+__device__ __forceinline__ void load_link_r12<WL_F16>(cx<float> (&w)[9], const void* base, long long Vh,
+                                                      int d, long long i)
+{
+    const uint4 t = ((const uint4*)base)[(long long)d * Vh + i];
+    const uint2 u = ((const uint2*)((const uint4*)base + 8 * Vh))[(long long)d * Vh + i];
+    const float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), e = h2f(t.w), f = h2f(u.x), h = h2f(u.y);
+    w[0] = {a.x, a.y};
+    w[1] = {b.x, b.y};
+    w[2] = {c.x, c.y};
+    w[3] = {e.x, e.y};
+    w[4] = {f.x, f.y};
+    w[5] = {h.x, h.y};
+    su3_third_row(w);
+}
+
+// FP16 spinor without its per-site norm applied (the caller scales the
+// projected half spinor instead: 12 multiplies per hop instead of 24)
+__device__ __forceinline__ void load_spinor_ro_f16_unscaled(cx<float> (&v)[12], float& nrm,
+                                                           const void* base, long long Vh, long long i)
+{
+    const uint4* p = (const uint4*)base;
+    nrm = __ldg((const float*)(p + 3 * Vh) + i);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const uint4 t = __ldg(p + k * Vh + i);
+        const float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), d = h2f(t.w);
+        v[4 * k + 0] = {a.x, a.y};
+        v[4 * k + 1] = {b.x, b.y};
+        v[4 * k + 2] = {c.x, c.y};
+        v[4 * k + 3] = {d.x, d.y};
+    }
+}
+
+// the projected half spinor of the neighbour spinor at index nb
+template <int P, int MU, int S>
+__device__ __forceinline__ void load_project(cx<typename Prec<P>::real> (&h0)[3],
+                                             cx<typename Prec<P>::real> (&h1)[3], const void* in,
+                                             long long Vh, int nb)
 {
     using T = typename Prec<P>::real;
-    if constexpr (P == WL_F64 || P == WL_DF64) {
-        cx<T> h0[3], h1[3];
-        {
-            cx<T> q[12];
-            load_spinor_ro<P>(q, in, Vh, nb);
-            project<MU, S>(h0, h1, q);
+    cx<T> q[12];
+    if constexpr (P == WL_F16) {
+        float nrm;
+        load_spinor_ro_f16_unscaled(q, nrm, in, Vh, nb);
+        project<MU, S>(h0, h1, q);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            h0[c] = nrm * h0[c];
+            h1[c] = nrm * h1[c];
         }
+    } else {
+        load_spinor_ro<P>(q, in, Vh, nb);
+        project<MU, S>(h0, h1, q);
+    }
+}
+
+template <int P, int D, int MU, int S, int LF>
+__device__ __forceinline__ void hop_one(cx<typename Prec<P>::real> (&acc)[12], const void* in,
+                                        long long Vh, int nb, const void* links, long long lVh,
+                                        int li, unsigned cross, const cx<float>* ph)
+{
+    using T = typename Prec<P>::real;
+    if constexpr (LF == 1) {
+        cx<T> h0[3], h1[3], W[9];
+        load_project<P, MU, S>(h0, h1, in, Vh, nb);
+        if (cross & (1u << D)) {  // boundary phase: phi forward, conj(phi) backward
+            const cx<T> f = (D & 1) ? conj(ph[MU]) : ph[MU];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                h0[c] = f * h0[c];
+                h1[c] = f * h1[c];
+            }
+        }
+        load_link_r12<P>(W, links, lVh, D, li);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            reconstruct<MU, S>(acc, a, dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h0),
+                               dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h1));
+    } else if constexpr (P == WL_F64) {  // links one row at a time: fewer live registers
+        cx<T> h0[3], h1[3];
+        load_project<P, MU, S>(h0, h1, in, Vh, nb);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             cx<T> w[3];
             load_link_row<P>(w, links, lVh, D, li, a);
             reconstruct<MU, S>(acc, a, dot3(w[0], w[1], w[2], h0), dot3(w[0], w[1], w[2], h1));
         }
-    } else {
+    } else if constexpr (P == WL_F16) {
+        cx<T> h0[3], h1[3], W[9];
+        load_project<P, MU, S>(h0, h1, in, Vh, nb);
+        load_link<P>(W, links, lVh, D, li);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            reconstruct<MU, S>(acc, a, dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h0),
+                               dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h1));
+    } else {  // FP32 (df64 takes hop_site_loop instead)
         cx<T> q[12], W[9];
         load_spinor_ro<P>(q, in, Vh, nb);
         load_link<P>(W, links, lVh, D, li);
@@ -225,27 +388,108 @@ __device__ __forceinline__ void hop_one(cx<typename Prec<P>::real> (&acc)[12], c
     }
 }
 
-// acc = H_{p,1-p} in at the output site whose neighbours are nb.  The links
-// are read from planes of stride lVh at index li (the global link field, or a
-// tile of it staged in shared memory).  DAG flips the projector signs.
+// i^k x for k = 0..3 (multiplication by 1, i, -1, -i: swaps and negations,
+// exact in every arithmetic type)
+template <typename T>
+__device__ __forceinline__ cx<T> mul_ik(cx<T> x, int k)
+{
+    const bool swap = k & 1, neg_re = k == 1 || k == 2, neg_im = k >= 2;
+    cx<T> r = swap ? cx<T>{x.im, x.re} : x;
+    if (neg_re) r.re = -r.re;
+    if (neg_im) r.im = -r.im;
+    return r;
+}
+
+// The projection / reconstruction table above as data, for a runtime loop
+// over the hops: per direction mu (12 bits each), with S = +1,
+//   h0 = psi0 + i^k0 psi[2 + a0],  h1 = psi1 + i^k1 psi[2 + a1],
+//   row 2 += i^k2 u[b2],           row 3 += i^k3 u[b3]
+// (bits: a0 | k0 << 1 | a1 << 3 | k1 << 4 | b2 << 6 | k2 << 7 | b3 << 9 | k3 << 10);
+// S = -1 adds 2 to every k.
+__device__ __forceinline__ unsigned hop_code(int mu)
+{
+    constexpr unsigned long long kTable =
+        (1ull | 1ull << 1 | 0ull << 3 | 1ull << 4 | 1ull << 6 | 3ull << 7 | 0ull << 9 | 3ull << 10) |
+        (1ull | 2ull << 1 | 0ull << 3 | 0ull << 4 | 1ull << 6 | 0ull << 7 | 0ull << 9 | 2ull << 10) << 12 |
+        (0ull | 1ull << 1 | 1ull << 3 | 3ull << 4 | 0ull << 6 | 3ull << 7 | 1ull << 9 | 1ull << 10) << 24 |
+        (0ull | 0ull << 1 | 1ull << 3 | 0ull << 4 | 0ull << 6 | 0ull << 7 | 1ull << 9 | 0ull << 10) << 36;
+    return (unsigned)(kTable >> (12 * mu)) & 0xfffu;
+}
+
+// The double-float type is ALU-bound, and its arithmetic makes a fully
+// unrolled eight-hop body too large for the instruction cache (ncu: "no
+// instruction" stalls dominated; the loop form runs 2.7x faster).  It runs the
+// hops as a loop with the spin structure from hop_code(), the link one row at
+// a time.  (Plain FP64 keeps the unrolled form: looped it ran 25 % slower.)
 template <int P, bool DAG>
-__device__ __forceinline__ void hop_site(cx<typename Prec<P>::real> (&acc)[12], const int (&nb)[8],
-                                         long long Vh, const void* in, const void* links,
-                                         long long lVh, int li)
+__device__ __forceinline__ void hop_site_loop(cx<typename Prec<P>::real> (&acc)[12], const int (&nb)[8],
+                                              long long Vh, const void* in, const void* links,
+                                              long long lVh, int li)
 {
     using T = typename Prec<P>::real;
 #pragma unroll
     for (int c = 0; c < 12; ++c) acc[c] = {(T)0, (T)0};
-    constexpr int F = DAG ? +1 : -1;  // forward projector sign
-    constexpr int B = -F;             // backward projector sign
-    hop_one<P, 0, 0, F>(acc, in, Vh, nb[0], links, lVh, li);
-    hop_one<P, 1, 0, B>(acc, in, Vh, nb[1], links, lVh, li);
-    hop_one<P, 2, 1, F>(acc, in, Vh, nb[2], links, lVh, li);
-    hop_one<P, 3, 1, B>(acc, in, Vh, nb[3], links, lVh, li);
-    hop_one<P, 4, 2, F>(acc, in, Vh, nb[4], links, lVh, li);
-    hop_one<P, 5, 2, B>(acc, in, Vh, nb[5], links, lVh, li);
-    hop_one<P, 6, 3, F>(acc, in, Vh, nb[6], links, lVh, li);
-    hop_one<P, 7, 3, B>(acc, in, Vh, nb[7], links, lVh, li);
+#pragma unroll 1
+    for (int d = 0; d < 8; ++d) {
+        const unsigned code = hop_code(d >> 1);
+        // forward hops use Eq. 1's (1 - gamma) (S = -1), backward (1 + gamma);
+        // the adjoint flips both
+        const int sflip = ((d & 1) ? DAG == false : DAG == true) ? 0 : 2;
+        const int a0 = code & 1, k0 = ((code >> 1) + sflip) & 3;
+        const int a1 = (code >> 3) & 1, k1 = ((code >> 4) + sflip) & 3;
+        const int b2 = (code >> 6) & 1, k2 = ((code >> 7) + sflip) & 3;
+        const int b3 = (code >> 9) & 1, k3 = ((code >> 10) + sflip) & 3;
+        cx<T> h0[3], h1[3];
+        {
+            cx<T> q[12];
+            load_spinor_ro<P>(q, in, Vh, nb[d]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                h0[c] = q[c] + mul_ik(a0 ? q[9 + c] : q[6 + c], k0);
+                h1[c] = q[3 + c] + mul_ik(a1 ? q[9 + c] : q[6 + c], k1);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cx<T> w[3];
+            load_link_row<P>(w, links, lVh, d, li, a);
+            const cx<T> u0 = dot3(w[0], w[1], w[2], h0), u1 = dot3(w[0], w[1], w[2], h1);
+            acc[a] = acc[a] + u0;
+            acc[3 + a] = acc[3 + a] + u1;
+            acc[6 + a] = acc[6 + a] + mul_ik(b2 ? u1 : u0, k2);
+            acc[9 + a] = acc[9 + a] + mul_ik(b3 ? u1 : u0, k3);
+        }
+    }
+}
+
+// acc = H_{p,1-p} in at the output site whose neighbours are nb.  The links
+// are read from planes of stride lVh at index li (the global link field, or a
+// tile of it staged in shared memory).  DAG flips the projector signs.
+// With LF = 1 the links are the compressed form and `cross` / `ph` give the
+// boundary-crossing hops and the four boundary phases.
+template <int P, bool DAG, int LF = 0>
+__device__ __forceinline__ void hop_site(cx<typename Prec<P>::real> (&acc)[12], const int (&nb)[8],
+                                         long long Vh, const void* in, const void* links,
+                                         long long lVh, int li, unsigned cross = 0,
+                                         const cx<float>* ph = nullptr)
+{
+    using T = typename Prec<P>::real;
+    if constexpr (P == WL_DF64 && LF == 0) {
+        hop_site_loop<P, DAG>(acc, nb, Vh, in, links, lVh, li);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = {(T)0, (T)0};
+        constexpr int F = DAG ? +1 : -1;  // forward projector sign
+        constexpr int B = -F;             // backward projector sign
+        hop_one<P, 0, 0, F, LF>(acc, in, Vh, nb[0], links, lVh, li, cross, ph);
+        hop_one<P, 1, 0, B, LF>(acc, in, Vh, nb[1], links, lVh, li, cross, ph);
+        hop_one<P, 2, 1, F, LF>(acc, in, Vh, nb[2], links, lVh, li, cross, ph);
+        hop_one<P, 3, 1, B, LF>(acc, in, Vh, nb[3], links, lVh, li, cross, ph);
+        hop_one<P, 4, 2, F, LF>(acc, in, Vh, nb[4], links, lVh, li, cross, ph);
+        hop_one<P, 5, 2, B, LF>(acc, in, Vh, nb[5], links, lVh, li, cross, ph);
+        hop_one<P, 6, 3, F, LF>(acc, in, Vh, nb[6], links, lVh, li, cross, ph);
+        hop_one<P, 7, 3, B, LF>(acc, in, Vh, nb[7], links, lVh, li, cross, ph);
+    }
 }
 
 struct HopArgs {
@@ -257,6 +501,7 @@ struct HopArgs {
     const char* x2[2];
     const char* w[2];
     const void* cl[2];  // clover matrix (A or A^-1) per launch parity, see CL below
+    cx<float> ph[4];    // boundary phases (used by the compressed-link kernels)
     long long rs_in, rs_out, rs_x1, rs_x2, rs_w;
     double a, b1;
     int parity0, nparity, blocks_per_parity;
@@ -343,30 +588,11 @@ __device__ __forceinline__ void epilogue(cx<typename Prec<P>::real> (&acc)[12], 
 static constexpr int kTile = 32;
 static constexpr int kMaxRhsLaunch = 32;
 
-template <int P>
-struct LinkPlanes;  // the link field as 16-byte planes plus narrower planes
-template <>
-struct LinkPlanes<WL_F64> {
-    static constexpr int n16 = 72, nsmall = 0, small_bytes = 8;
-};
-template <>
-struct LinkPlanes<WL_F32> {
-    static constexpr int n16 = 32, nsmall = 8, small_bytes = 8;
-};
-template <>
-struct LinkPlanes<WL_DF64> {
-    static constexpr int n16 = 72, nsmall = 0, small_bytes = 8;
-};
-template <>
-struct LinkPlanes<WL_F16> {
-    static constexpr int n16 = 16, nsmall = 8, small_bytes = 4;
-};
-
 // Copy the links of sites [base, base + n) into a kTile-stride tile.
-template <int P>
+template <int P, int LF = 0>
 __device__ __forceinline__ void stage_links(char* sm, const char* gl, long long Vh, int base, int n)
 {
-    using LP = LinkPlanes<P>;
+    using LP = LinkLayout<P, LF>;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
     for (int e = tid; e < LP::n16 * kTile; e += nt) {
         const int q = e / kTile, j = e - q * kTile;
@@ -414,10 +640,10 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <int P>
+template <int P, int LF = 0>
 __device__ __forceinline__ void stage_links_async(char* sm, const char* gl, long long Vh, int base, int n)
 {
-    using LP = LinkPlanes<P>;
+    using LP = LinkLayout<P, LF>;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
     for (int e = tid; e < LP::n16 * kTile; e += nt) {
         const int q = e / kTile, j = e - q * kTile;

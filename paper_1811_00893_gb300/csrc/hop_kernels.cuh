@@ -47,22 +47,25 @@ struct MinBlocks {
     static constexpr int value = DOT && base > 2 ? 2 : base;  // the reducing loop needs more
 };
 
-template <int P, bool DAG, bool DOT, int CL>
+template <int P, bool DAG, bool DOT, int CL, int LF>
 __device__ __forceinline__ void hop_kernel_site(const HopArgs& A, int rhs, int pidx, int i,
                                                 typename Prec<P>::real (&part)[3])
 {
     using T = typename Prec<P>::real;
     cx<T> acc[12];
     int nb[8];
-    neighbours(A.g, A.parity0 + pidx, i, nb);
-    hop_site<P, DAG>(acc, nb, A.g.Vh, A.in[pidx] + rhs * A.rs_in, A.links[pidx], A.g.Vh, i);
+    unsigned cross = 0;
+    if constexpr (LF == 1) neighbours(A.g, A.parity0 + pidx, i, nb, cross);
+    else neighbours(A.g, A.parity0 + pidx, i, nb);
+    hop_site<P, DAG, LF>(acc, nb, A.g.Vh, A.in[pidx] + rhs * A.rs_in, A.links[pidx], A.g.Vh, i, cross,
+                         A.ph);
     T pt[3] = {0, 0, 0};
     epilogue<P, DOT, CL>(acc, A, pidx, rhs, i, pt);
     if (DOT)
         for (int k = 0; k < 3; ++k) part[k] += pt[k];
 }
 
-template <int P, bool DAG, bool DOT, int CL>
+template <int P, bool DAG, bool DOT, int CL, int LF>
 __global__ void __launch_bounds__(256, (MinBlocks<P, DOT>::value)) hop_kernel(const HopArgs A)
 {
     const int rhs = blockIdx.y;
@@ -73,13 +76,13 @@ __global__ void __launch_bounds__(256, (MinBlocks<P, DOT>::value)) hop_kernel(co
     if constexpr (!DOT) {  // one site per thread; the block's parity is fixed
         const int pidx = blockIdx.x / A.blocks_per_parity;
         const int i = (blockIdx.x - pidx * A.blocks_per_parity) * blockDim.x + threadIdx.x;
-        if (i < A.g.Vh) hop_kernel_site<P, DAG, DOT, CL>(A, rhs, pidx, i, tpart);
+        if (i < A.g.Vh) hop_kernel_site<P, DAG, DOT, CL, LF>(A, rhs, pidx, i, tpart);
         (void)total;
     } else {
         for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < total;
              j += (long long)gridDim.x * blockDim.x) {
             const int pidx = j >= A.g.Vh ? 1 : 0;
-            hop_kernel_site<P, DAG, DOT, CL>(A, rhs, pidx, (int)(j - pidx * A.g.Vh), tpart);
+            hop_kernel_site<P, DAG, DOT, CL, LF>(A, rhs, pidx, (int)(j - pidx * A.g.Vh), tpart);
         }
         double part[3] = {(double)tpart[0], (double)tpart[1], (double)tpart[2]};
         __shared__ double sh[3 * 32];
@@ -94,7 +97,7 @@ __global__ void __launch_bounds__(256, (MinBlocks<P, DOT>::value)) hop_kernel(co
     }
 }
 
-template <int P, bool DAG, bool DOT, int CL>
+template <int P, bool DAG, bool DOT, int CL, int LF>
 __global__ void __launch_bounds__(256, (MinBlocks<P, DOT>::value)) hop_mrhs_kernel(const HopArgs A, int nrhs)
 {
     using T = typename Prec<P>::real;
@@ -103,19 +106,23 @@ __global__ void __launch_bounds__(256, (MinBlocks<P, DOT>::value)) hop_mrhs_kern
     const int p = A.parity0 + pidx;
     const int base = (blockIdx.x - pidx * A.blocks_per_parity) * kTile;
     const int n = (int)min((long long)kTile, A.g.Vh - base);
-    stage_links<P>(smem, (const char*)A.links[pidx], A.g.Vh, base, n);
-    double* bpart = (double*)(smem + Prec<P>::link_bytes * kTile);
+    stage_links<P, LF>(smem, (const char*)A.links[pidx], A.g.Vh, base, n);
+    double* bpart = (double*)(smem + LinkLayout<P, LF>::bytes * kTile);
     __syncthreads();
     const int lane = threadIdx.x, i = base + lane;
     const bool valid = lane < n;
     int nb[8];
-    if (valid) neighbours(A.g, p, i, nb);
+    unsigned cross = 0;
+    if (valid) {
+        if constexpr (LF == 1) neighbours(A.g, p, i, nb, cross);
+        else neighbours(A.g, p, i, nb);
+    }
     for (int r = threadIdx.y; r < nrhs; r += blockDim.y) {
         const bool act = !A.active || A.active[r * A.active_stride] != 0;  // warp-uniform
         T part[3] = {0, 0, 0};
         if (act && valid) {
             cx<T> acc[12];
-            hop_site<P, DAG>(acc, nb, A.g.Vh, A.in[pidx] + r * A.rs_in, smem, kTile, lane);
+            hop_site<P, DAG, LF>(acc, nb, A.g.Vh, A.in[pidx] + r * A.rs_in, smem, kTile, lane, cross, A.ph);
             epilogue<P, DOT, CL>(acc, A, pidx, r, i, part);
         }
         if (DOT) {  // 32 sites in FP32 (FP64 for the wide types), then FP64 from here on
@@ -145,12 +152,12 @@ __global__ void __launch_bounds__(256, (MinBlocks<P, DOT>::value)) hop_mrhs_kern
 // block already copies the next tile's links into the other half of a
 // double buffer with cp.async.  Partial sums are written per tile, as in
 // hop_mrhs_kernel, and added up in tile order by the finishing launch.
-template <int P, bool DAG, bool DOT, int CL>
+template <int P, bool DAG, bool DOT, int CL, int LF>
 __global__ void __launch_bounds__(256, 2) hop_mrhs_pipe_kernel(const HopArgs A, int nrhs, int ntiles)
 {
     using T = typename Prec<P>::real;
     extern __shared__ __align__(16) char smem[];
-    constexpr int kBuf = (int)Prec<P>::link_bytes * kTile;
+    constexpr int kBuf = LinkLayout<P, LF>::bytes * kTile;
     double* bpart = (double*)(smem + 2 * kBuf);
     const int lane = threadIdx.x;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
@@ -164,7 +171,7 @@ __global__ void __launch_bounds__(256, 2) hop_mrhs_pipe_kernel(const HopArgs A, 
     {
         int pidx, base, n;
         tile_at(tile, pidx, base, n);
-        stage_links_async<P>(smem, (const char*)A.links[pidx], A.g.Vh, base, n);
+        stage_links_async<P, LF>(smem, (const char*)A.links[pidx], A.g.Vh, base, n);
         cp_async_commit();
     }
     for (int it = 0; tile < ntiles; ++it) {
@@ -172,7 +179,7 @@ __global__ void __launch_bounds__(256, 2) hop_mrhs_pipe_kernel(const HopArgs A, 
         if (next < ntiles) {  // prefetch the next tile into the other buffer
             int pidx, base, n;
             tile_at(next, pidx, base, n);
-            stage_links_async<P>(smem + ((it + 1) & 1) * kBuf, (const char*)A.links[pidx], A.g.Vh,
+            stage_links_async<P, LF>(smem + ((it + 1) & 1) * kBuf, (const char*)A.links[pidx], A.g.Vh,
                                  base, n);
         }
         cp_async_commit();  // (an empty group on the last tile)
@@ -185,13 +192,18 @@ __global__ void __launch_bounds__(256, 2) hop_mrhs_pipe_kernel(const HopArgs A, 
         const int i = base + lane;
         const bool valid = lane < n;
         int nb[8];
-        if (valid) neighbours(A.g, p, i, nb);
+        unsigned cross = 0;
+        if (valid) {
+            if constexpr (LF == 1) neighbours(A.g, p, i, nb, cross);
+            else neighbours(A.g, p, i, nb);
+        }
         for (int r = threadIdx.y; r < nrhs; r += blockDim.y) {
             const bool act = !A.active || A.active[r * A.active_stride] != 0;  // warp-uniform
             T part[3] = {0, 0, 0};
             if (act && valid) {
                 cx<T> acc[12];
-                hop_site<P, DAG>(acc, nb, A.g.Vh, A.in[pidx] + r * A.rs_in, links, kTile, lane);
+                hop_site<P, DAG, LF>(acc, nb, A.g.Vh, A.in[pidx] + r * A.rs_in, links, kTile, lane, cross,
+                                     A.ph);
                 epilogue<P, DOT, CL>(acc, A, pidx, r, i, part);
             }
             if (DOT) {
@@ -215,8 +227,9 @@ __global__ void __launch_bounds__(256, 2) hop_mrhs_pipe_kernel(const HopArgs A, 
     }
 }
 
-// Host-side launchers of one clover mode.
-template <int CL>
+// Host-side launchers of one clover mode and link format (LF = 1 exists for
+// FP32 and FP16 only; other precisions are never requested with it).
+template <int CL, int LF = 0>
 struct HopKernels {
     static void single(int prec, bool dagger, bool dot, const HopArgs& A, dim3 grid, int block,
                        cudaStream_t s);
@@ -230,101 +243,105 @@ struct HopKernels {
     static const void* reducing(int prec, bool dagger);
 };
 
-template <int CL, int P>
+template <int CL, int LF, int P>
 static void hop_single_p(bool dagger, bool dot, const HopArgs& A, dim3 grid, int block, cudaStream_t s)
 {
     if (dagger) {
-        if (dot) hop_kernel<P, true, true, CL><<<grid, block, 0, s>>>(A);
-        else hop_kernel<P, true, false, CL><<<grid, block, 0, s>>>(A);
+        if (dot) hop_kernel<P, true, true, CL, LF><<<grid, block, 0, s>>>(A);
+        else hop_kernel<P, true, false, CL, LF><<<grid, block, 0, s>>>(A);
     } else {
-        if (dot) hop_kernel<P, false, true, CL><<<grid, block, 0, s>>>(A);
-        else hop_kernel<P, false, false, CL><<<grid, block, 0, s>>>(A);
+        if (dot) hop_kernel<P, false, true, CL, LF><<<grid, block, 0, s>>>(A);
+        else hop_kernel<P, false, false, CL, LF><<<grid, block, 0, s>>>(A);
     }
 }
 
-template <int CL, int P>
+template <int CL, int LF, int P>
 static void hop_multi_p(bool dagger, bool dot, const HopArgs& A, int nrhs, dim3 grid, dim3 block,
                         size_t smem, cudaStream_t s)
 {
     if (dagger) {
-        if (dot) hop_mrhs_kernel<P, true, true, CL><<<grid, block, smem, s>>>(A, nrhs);
-        else hop_mrhs_kernel<P, true, false, CL><<<grid, block, smem, s>>>(A, nrhs);
+        if (dot) hop_mrhs_kernel<P, true, true, CL, LF><<<grid, block, smem, s>>>(A, nrhs);
+        else hop_mrhs_kernel<P, true, false, CL, LF><<<grid, block, smem, s>>>(A, nrhs);
     } else {
-        if (dot) hop_mrhs_kernel<P, false, true, CL><<<grid, block, smem, s>>>(A, nrhs);
-        else hop_mrhs_kernel<P, false, false, CL><<<grid, block, smem, s>>>(A, nrhs);
+        if (dot) hop_mrhs_kernel<P, false, true, CL, LF><<<grid, block, smem, s>>>(A, nrhs);
+        else hop_mrhs_kernel<P, false, false, CL, LF><<<grid, block, smem, s>>>(A, nrhs);
     }
 }
 
-template <int CL, int P>
+template <int CL, int LF, int P>
 static void hop_pipe_p(bool dagger, bool dot, const HopArgs& A, int nrhs, int ntiles, dim3 grid,
                        dim3 block, size_t smem, cudaStream_t s)
 {
     if (dagger) {
-        if (dot) hop_mrhs_pipe_kernel<P, true, true, CL><<<grid, block, smem, s>>>(A, nrhs, ntiles);
-        else hop_mrhs_pipe_kernel<P, true, false, CL><<<grid, block, smem, s>>>(A, nrhs, ntiles);
+        if (dot) hop_mrhs_pipe_kernel<P, true, true, CL, LF><<<grid, block, smem, s>>>(A, nrhs, ntiles);
+        else hop_mrhs_pipe_kernel<P, true, false, CL, LF><<<grid, block, smem, s>>>(A, nrhs, ntiles);
     } else {
-        if (dot) hop_mrhs_pipe_kernel<P, false, true, CL><<<grid, block, smem, s>>>(A, nrhs, ntiles);
-        else hop_mrhs_pipe_kernel<P, false, false, CL><<<grid, block, smem, s>>>(A, nrhs, ntiles);
+        if (dot) hop_mrhs_pipe_kernel<P, false, true, CL, LF><<<grid, block, smem, s>>>(A, nrhs, ntiles);
+        else hop_mrhs_pipe_kernel<P, false, false, CL, LF><<<grid, block, smem, s>>>(A, nrhs, ntiles);
     }
 }
 
-template <int CL, int P>
+template <int CL, int LF, int P>
 static const void* pipe_kernel_p(bool dagger, bool dot)
 {
     if (dagger)
-        return dot ? (const void*)hop_mrhs_pipe_kernel<P, true, true, CL>
-                   : (const void*)hop_mrhs_pipe_kernel<P, true, false, CL>;
-    return dot ? (const void*)hop_mrhs_pipe_kernel<P, false, true, CL>
-               : (const void*)hop_mrhs_pipe_kernel<P, false, false, CL>;
+        return dot ? (const void*)hop_mrhs_pipe_kernel<P, true, true, CL, LF>
+                   : (const void*)hop_mrhs_pipe_kernel<P, true, false, CL, LF>;
+    return dot ? (const void*)hop_mrhs_pipe_kernel<P, false, true, CL, LF>
+               : (const void*)hop_mrhs_pipe_kernel<P, false, false, CL, LF>;
 }
 
-template <int CL>
-void HopKernels<CL>::pipe(int prec, bool dagger, bool dot, const HopArgs& A, int nrhs, int ntiles,
+template <int CL, int LF>
+void HopKernels<CL, LF>::pipe(int prec, bool dagger, bool dot, const HopArgs& A, int nrhs, int ntiles,
                           dim3 grid, dim3 block, size_t smem, cudaStream_t s)
 {
-    if (prec == WL_F32) hop_pipe_p<CL, WL_F32>(dagger, dot, A, nrhs, ntiles, grid, block, smem, s);
-    else hop_pipe_p<CL, WL_F16>(dagger, dot, A, nrhs, ntiles, grid, block, smem, s);
+    if (prec == WL_F32) hop_pipe_p<CL, LF, WL_F32>(dagger, dot, A, nrhs, ntiles, grid, block, smem, s);
+    else hop_pipe_p<CL, LF, WL_F16>(dagger, dot, A, nrhs, ntiles, grid, block, smem, s);
 }
 
-template <int CL>
-const void* HopKernels<CL>::pipe_kernel(int prec, bool dagger, bool dot)
+template <int CL, int LF>
+const void* HopKernels<CL, LF>::pipe_kernel(int prec, bool dagger, bool dot)
 {
-    return prec == WL_F32 ? pipe_kernel_p<CL, WL_F32>(dagger, dot) : pipe_kernel_p<CL, WL_F16>(dagger, dot);
+    return prec == WL_F32 ? pipe_kernel_p<CL, LF, WL_F32>(dagger, dot) : pipe_kernel_p<CL, LF, WL_F16>(dagger, dot);
 }
 
-template <int CL>
-void HopKernels<CL>::single(int prec, bool dagger, bool dot, const HopArgs& A, dim3 grid, int block,
+template <int CL, int LF>
+void HopKernels<CL, LF>::single(int prec, bool dagger, bool dot, const HopArgs& A, dim3 grid, int block,
                             cudaStream_t s)
 {
-    switch (prec) {
-        case WL_F64: hop_single_p<CL, WL_F64>(dagger, dot, A, grid, block, s); break;
-        case WL_F32: hop_single_p<CL, WL_F32>(dagger, dot, A, grid, block, s); break;
-        case WL_F16: hop_single_p<CL, WL_F16>(dagger, dot, A, grid, block, s); break;
-        default: hop_single_p<CL, WL_DF64>(dagger, dot, A, grid, block, s); break;
+    if (prec == WL_F32) hop_single_p<CL, LF, WL_F32>(dagger, dot, A, grid, block, s);
+    else if (prec == WL_F16) hop_single_p<CL, LF, WL_F16>(dagger, dot, A, grid, block, s);
+    else if constexpr (LF == 0) {
+        if (prec == WL_F64) hop_single_p<CL, LF, WL_F64>(dagger, dot, A, grid, block, s);
+        else hop_single_p<CL, LF, WL_DF64>(dagger, dot, A, grid, block, s);
     }
 }
 
-template <int CL>
-void HopKernels<CL>::multi(int prec, bool dagger, bool dot, const HopArgs& A, int nrhs, dim3 grid,
+template <int CL, int LF>
+void HopKernels<CL, LF>::multi(int prec, bool dagger, bool dot, const HopArgs& A, int nrhs, dim3 grid,
                            dim3 block, size_t smem, cudaStream_t s)
 {
-    switch (prec) {
-        case WL_F64: hop_multi_p<CL, WL_F64>(dagger, dot, A, nrhs, grid, block, smem, s); break;
-        case WL_F32: hop_multi_p<CL, WL_F32>(dagger, dot, A, nrhs, grid, block, smem, s); break;
-        case WL_F16: hop_multi_p<CL, WL_F16>(dagger, dot, A, nrhs, grid, block, smem, s); break;
-        default: hop_multi_p<CL, WL_DF64>(dagger, dot, A, nrhs, grid, block, smem, s); break;
+    if (prec == WL_F32) hop_multi_p<CL, LF, WL_F32>(dagger, dot, A, nrhs, grid, block, smem, s);
+    else if (prec == WL_F16) hop_multi_p<CL, LF, WL_F16>(dagger, dot, A, nrhs, grid, block, smem, s);
+    else if constexpr (LF == 0) {
+        if (prec == WL_F64) hop_multi_p<CL, LF, WL_F64>(dagger, dot, A, nrhs, grid, block, smem, s);
+        else hop_multi_p<CL, LF, WL_DF64>(dagger, dot, A, nrhs, grid, block, smem, s);
     }
 }
 
-template <int CL>
-const void* HopKernels<CL>::reducing(int prec, bool dagger)
+template <int CL, int LF>
+const void* HopKernels<CL, LF>::reducing(int prec, bool dagger)
 {
-    switch (prec) {
-        case WL_F64: return dagger ? (const void*)hop_kernel<WL_F64, true, true, CL> : (const void*)hop_kernel<WL_F64, false, true, CL>;
-        case WL_F32: return dagger ? (const void*)hop_kernel<WL_F32, true, true, CL> : (const void*)hop_kernel<WL_F32, false, true, CL>;
-        case WL_F16: return dagger ? (const void*)hop_kernel<WL_F16, true, true, CL> : (const void*)hop_kernel<WL_F16, false, true, CL>;
-        default: return dagger ? (const void*)hop_kernel<WL_DF64, true, true, CL> : (const void*)hop_kernel<WL_DF64, false, true, CL>;
+    if (prec == WL_F32)
+        return dagger ? (const void*)hop_kernel<WL_F32, true, true, CL, LF> : (const void*)hop_kernel<WL_F32, false, true, CL, LF>;
+    if (prec == WL_F16)
+        return dagger ? (const void*)hop_kernel<WL_F16, true, true, CL, LF> : (const void*)hop_kernel<WL_F16, false, true, CL, LF>;
+    if constexpr (LF == 0) {
+        if (prec == WL_F64)
+            return dagger ? (const void*)hop_kernel<WL_F64, true, true, CL, LF> : (const void*)hop_kernel<WL_F64, false, true, CL, LF>;
+        return dagger ? (const void*)hop_kernel<WL_DF64, true, true, CL, LF> : (const void*)hop_kernel<WL_DF64, false, true, CL, LF>;
     }
+    return nullptr;
 }
 
 }  // namespace wl

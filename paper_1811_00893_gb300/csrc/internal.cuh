@@ -48,6 +48,8 @@ struct wl_gauge_s {
     int num_sms;
     // [prec][out parity]; prec 3 is the internal df64 copy used by the outer corrections
     void* links[4][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    // compressed (two-row) copies of the FP32 / FP16 links, when requested (WL_LINKS_R12)
+    void* links_r12[4][2] = {};
     // grid-reduction scratch
     wl::RedScratch red = {nullptr, nullptr, 0};
     int red_slots = 0;

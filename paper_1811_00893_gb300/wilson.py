@@ -25,6 +25,10 @@ ERR_NAMES = {0: "WL_OK", -1: "WL_ERR_ARG", -2: "WL_ERR_CUDA", -3: "WL_ERR_NOT_CO
              -4: "WL_ERR_BREAKDOWN", -5: "WL_ERR_NAN", -6: "WL_ERR_TIMEOUT", -7: "WL_ERR_STATE"}
 
 
+#: wl_gauge_create flag: also keep two-row (reconstruct-12) FP32/FP16 links
+WL_LINKS_R12 = 1 << 8
+
+
 def prec_mask(*precs) -> int:
     m = 0
     for p in precs:
@@ -280,12 +284,13 @@ class Gauge:
     """Owns a wl_gauge handle; `fields(prec, nrhs)` allocates internal fields."""
 
     def __init__(self, dims, kappa, U: torch.Tensor, precs=("f64", "f32", "f16"),
-                 bc=(1, 1, 1, -1), stream=None):
+                 bc=(1, 1, 1, -1), stream=None, r12: bool = False):
         self.dims = tuple(int(d) for d in dims)
         self.kappa = float(kappa)
         self.bc = tuple(bc)
         self.lat = lattice(dims, kappa, bc)
-        self.handle = wl_gauge_create(self.lat, U, prec_mask(*precs), stream)
+        mask = prec_mask(*precs) | (WL_LINKS_R12 if r12 else 0)
+        self.handle = wl_gauge_create(self.lat, U, mask, stream)
         self.Vh = wl_half_volume(self.handle)
 
     def field(self, prec, nrhs: int = 1, nhalf: int = 1) -> torch.Tensor:
