@@ -81,8 +81,13 @@ __global__ void __launch_bounds__(256) batch_hop_kernel(const BatchArgs B)
             // a lattice whose systems are all inactive (converged, or between
             // rounds) needs neither its links nor any arithmetic
             int any = 0;
-            if (it < B.total_items)
-                for (int r = 0; r < B.lats[lo].nrhs && !any; ++r) any = B.lats[lo].sc[r].active != 0;
+            if (it < B.total_items) {
+                const BLat& Lq = B.lats[lo];
+                for (int r = 0; r < Lq.nrhs && !any; ++r) any = Lq.sc[r].active != 0;
+                // move the counter past the rest of an idle lattice's items at
+                // once (every item in between belongs to it)
+                if (!any) atomicMax(&B.queue[0], (unsigned)(Lq.item0 + Lq.nitems));
+            }
             s_any = any;
         }
         __syncthreads();
@@ -624,12 +629,18 @@ extern "C" int wilson_solve_batch(int nlat, const wl_gauge* gs, double* const* x
         }
         if (all_done) break;
         if (!any_iter) continue;
-        int k = chunk;
+        // within every lattice's iteration cap; as long as the lattice that
+        // predicts the most iterations needs (the others skip once done)
+        int k = chunk, wanted = 0;
         for (int l = 0; l < nlat; ++l)
-            if (phase[l] == ITER) k = std::min(k, st[l].budget());
+            if (phase[l] == ITER) {
+                k = std::min(k, st[l].cap());
+                wanted = std::max(wanted, st[l].want());
+            }
+        if (wanted > 0) k = std::min(k, wanted);
         if (k <= 0) {  // a lattice ran out of iterations: end its round
             for (int l = 0; l < nlat; ++l)
-                if (phase[l] == ITER && st[l].budget() <= 0) {
+                if (phase[l] == ITER && st[l].cap() <= 0) {
                     WL_TRY(st[l].finish_round());
                     phase[l] = PLAN;
                 }

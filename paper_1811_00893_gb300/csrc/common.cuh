@@ -440,6 +440,26 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double* sh)
     }
 }
 
+// Block sum of per-warp totals already formed in a narrower type: lane 0 of
+// every warp holds its warp's total in v; the result is valid in thread 0.
+// (The kernels sum their sites in the arithmetic type, then go to FP64 at
+// the warp level: GB300 runs FP64 at 1/64 of the FP32 rate.)
+template <int N>
+__device__ __forceinline__ void block_sum_warps(double (&v)[N], double* sh)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) sh[k * 32 + w] = v[k];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[k] = lane < nw ? sh[k * 32 + lane] : 0.0;
+        warp_sum<N>(v);
+    }
+}
+
 // This thread's share of the sum of nblocks partial N-tuples (stride N),
 // four independent loads in flight so the loop is not one L2 latency per step.
 template <int N>

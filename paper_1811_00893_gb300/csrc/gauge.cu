@@ -567,6 +567,7 @@ extern "C" int wl_timing_read(wl_gauge g, int prec, double* ms, long long* launc
     long long n = 0;
     for (size_t k = 0; k < t.used; ++k) {
         if (prec >= 0 && t.prec[k] != prec) continue;
+        if (t.bytes[k] < 0.0) continue;  // a launch that found no work (solver chunk tail)
         ++n;
         WL_CUDA(cudaEventSynchronize(t.stop[k]));
         float e = 0.f;

@@ -84,9 +84,14 @@ __global__ void __launch_bounds__(256, (MinBlocks<P, DOT>::value)) hop_kernel(co
             const int pidx = j >= A.g.Vh ? 1 : 0;
             hop_kernel_site<P, DAG, DOT, CL, LF>(A, rhs, pidx, (int)(j - pidx * A.g.Vh), tpart);
         }
-        double part[3] = {(double)tpart[0], (double)tpart[1], (double)tpart[2]};
+        // warp totals in the arithmetic type (FP32 for the narrow types), FP64 from there
+        typename RedType<T>::type wp[3] = {(typename RedType<T>::type)tpart[0],
+                                           (typename RedType<T>::type)tpart[1],
+                                           (typename RedType<T>::type)tpart[2]};
+        warp_sum<3>(wp);
+        double part[3] = {(double)wp[0], (double)wp[1], (double)wp[2]};
         __shared__ double sh[3 * 32];
-        block_sum<3>(part, sh);
+        block_sum_warps<3>(part, sh);
         double tot[3];
         if (grid_sum<3>(part, tot, A.red, rhs, gridDim.x, blockIdx.x, sh)) {
             double* o = A.dot_out + (long long)rhs * A.dot_stride;

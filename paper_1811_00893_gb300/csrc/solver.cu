@@ -168,8 +168,12 @@ __global__ void __launch_bounds__(256) update_xr_kernel(char* x, Vec2 vx, char* 
                               dc, pt);
         for (int k = 0; k < 3; ++k) tpart[k] += pt[k];
     }
-    double part[3] = {(double)tpart[0], (double)tpart[1], (double)tpart[2]};
-    block_sum<3>(part, sh);
+    typename RedType<T>::type wp[3] = {(typename RedType<T>::type)tpart[0],
+                                       (typename RedType<T>::type)tpart[1],
+                                       (typename RedType<T>::type)tpart[2]};
+    warp_sum<3>(wp);  // warp totals in the arithmetic type, FP64 from there
+    double part[3] = {(double)wp[0], (double)wp[1], (double)wp[2]};
+    block_sum_warps<3>(part, sh);
     double tot[3];
     if (grid_sum<3>(part, tot, red, rhs, gridDim.x, blockIdx.x, sh)) advance_scalars(S, tot, dc);
 }
@@ -404,7 +408,39 @@ static int enqueue_iteration(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
 }
 
 // Run k iterations: a CUDA-graph replay when graph_k > 0, else eager launches.
+static int run_chunk_impl(wl_gauge g, Workspace* w, int nrhs, int k, bool use_graph, cudaStream_t s);
+
+// Run k iterations and remember what they were charged (see discount_chunk).
 int run_chunk(wl_gauge g, Workspace* w, int nrhs, int k, bool use_graph, cudaStream_t s)
+{
+    const long long b0 = g_bytes.load();
+    w->chunk_slot0 = g->timing.used;
+    const int rc = run_chunk_impl(g, w, nrhs, k, use_graph, s);
+    w->chunk_k = rc == WL_OK ? k : 0;
+    w->chunk_bytes = g_bytes.load() - b0;
+    w->chunk_slot1 = g->timing.used;
+    return rc;
+}
+
+// The last `skipped` iterations of the last chunk ran after every right-hand
+// side had stopped: their launches exited at once.  Take them out of the
+// algorithmic-byte counter and out of the per-launch timing records, so that
+// both describe the work done.
+void discount_chunk(wl_gauge g, Workspace* w, int skipped)
+{
+    if (skipped <= 0 || w->chunk_k <= 0) return;
+    if (skipped > w->chunk_k) skipped = w->chunk_k;
+    g_bytes.fetch_sub(w->chunk_bytes / w->chunk_k * skipped);
+    const size_t slots = w->chunk_slot1 - w->chunk_slot0;  // eager launches only
+    if (slots % (size_t)w->chunk_k == 0) {
+        const size_t per_iter = slots / (size_t)w->chunk_k;
+        for (size_t q = w->chunk_slot1 - per_iter * skipped; q < w->chunk_slot1; ++q)
+            g->timing.bytes[q] = -1.0;  // excluded by wl_timing_read
+    }
+    w->chunk_k = 0;
+}
+
+static int run_chunk_impl(wl_gauge g, Workspace* w, int nrhs, int k, bool use_graph, cudaStream_t s)
 {
     if (!use_graph) {
         for (int it = 0; it < k; ++it) WL_TRY(enqueue_iteration(g, w, nrhs, s));
@@ -676,6 +712,7 @@ int SolveState::begin(wl_gauge g_, double* x, const double* b, int nrhs_, const 
     x_user = x;
     WL_TRY(ensure_ws(g, P, nrhs, eo));
     w = g->ws;
+    w->chunk_k = 0;
     const long long V = 2 * g->geo.Vh;
     canon = (size_t)V * 24 * sizeof(double) * nrhs;
 
@@ -807,20 +844,61 @@ int SolveState::plan(bool* any_out)
     }
     *any_out = any != 0;
     if (!any) return WL_OK;
+    hist_rr.assign(nrhs, 0.0);
+    hist_it.assign(nrhs, 0);
+    next_k = 0;
     for (int k = 0; k < nrhs; ++k) {
         iters_before[k] = w->sc_h[k].iters;
         part[k] = in_inner[k] = w->mask_h[k];
         poisoned[k] = 0;
+        hist_rr[k] = rnorm2[k];
+        hist_it[k] = iters_before[k];
     }
     return inner_start(g, w, nrhs, target2.data(), delta2, s);
 }
 
-int SolveState::budget() const
+int SolveState::cap() const
 {
     int most = 0;  // iterations done by the furthest-along right-hand side of the round
     for (int k = 0; k < nrhs; ++k)
         if (in_inner[k] && w->sc_h[k].iters > most) most = w->sc_h[k].iters;
     return chunk < prm->maxiter - most ? chunk : prm->maxiter - most;
+}
+
+int SolveState::want() const { return next_k > 0 && next_k < chunk ? next_k : chunk; }
+
+int SolveState::budget() const { return std::min(cap(), want()); }
+
+// Length of the next chunk: the iterations each active right-hand side still
+// needs to reach its inner target (or its next reliable update), extrapolated
+// from the residual's decay over the last chunk; the longest of them, at most
+// one chunk.  Launching past convergence costs empty launches, stopping short
+// one more host round trip.
+void SolveState::predict_next()
+{
+    int most = 0;
+    bool any = false;
+    for (int k = 0; k < nrhs; ++k) {
+        if (!in_inner[k]) continue;
+        const Scal& S = w->sc_h[k];
+        const double rr = S.rr[2];
+        const int dit = S.iters - hist_it[k];
+        if (S.active) {
+            any = true;
+            int n = chunk;
+            if (dit > 0 && rr > 0.0 && hist_rr[k] > rr) {
+                const double rate = std::log(rr / hist_rr[k]) / dit;  // per iteration, < 0
+                double est = std::log(S.target2 / rr) / rate;
+                if (S.delta2 > 0.0 && S.r2_max > 0.0)
+                    est = std::min(est, std::log(S.delta2 * S.r2_max / rr) / rate);
+                n = est <= 1.0 ? 1 : (int)std::ceil(std::min(est, (double)chunk));
+            }
+            most = std::max(most, n);
+        }
+        hist_rr[k] = rr;
+        hist_it[k] = S.iters;
+    }
+    next_k = any ? most : 0;
 }
 
 int SolveState::read_scalars()
@@ -833,6 +911,12 @@ int SolveState::read_scalars()
 int SolveState::after_chunk(bool* alive)
 {
     int upd = 0, stopped = 0;
+    {  // iterations of the chunk that ran after every right-hand side had stopped
+        int did = 0;
+        for (int k = 0; k < nrhs; ++k)
+            if (in_inner[k]) did = std::max(did, w->sc_h[k].iters - hist_it[k]);
+        discount_chunk(g, w, w->chunk_k - did);
+    }
     for (int k = 0; k < nrhs; ++k) {
         w->mask_h[k] = 0;
         if (!in_inner[k]) continue;
@@ -870,6 +954,7 @@ int SolveState::after_chunk(bool* alive)
     bool a = false;
     for (int k = 0; k < nrhs; ++k) a |= in_inner[k] != 0;
     *alive = a;
+    if (a) predict_next();
     return WL_OK;
 }
 

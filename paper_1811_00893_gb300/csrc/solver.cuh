@@ -38,6 +38,10 @@ static const int kBlock = 256;     // vector-kernel block size
 
 struct Workspace {
     int inner = -1, nrhs = 0, eo = -1, nhalf = 0, xlo_prec = 0, outer = 0;
+    // the last chunk: iterations enqueued, bytes charged, timing slots used
+    int chunk_k = 0;
+    long long chunk_bytes = 0;
+    size_t chunk_slot0 = 0, chunk_slot1 = 0;
     size_t vb = 0;    // bytes of one inner vector (nhalf halves)
     size_t vb64 = 0;  // bytes of one FP64 vector (nhalf halves)
     size_t hb64 = 0;  // bytes of one FP64 half field
@@ -218,6 +222,7 @@ __device__ __forceinline__ void advance_scalars(Scal& S, const double (&tot)[3],
 int ensure_ws(wl_gauge g, int inner, int nrhs, int eo);
 int upload_mask(Workspace* w, int nrhs, cudaStream_t s);
 int run_chunk(wl_gauge g, Workspace* w, int nrhs, int k, bool use_graph, cudaStream_t s);
+void discount_chunk(wl_gauge g, Workspace* w, int skipped);
 int read_norms(Workspace* w, int nrhs, cudaStream_t s);
 int residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s);
 int true_residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s);
@@ -246,6 +251,10 @@ struct SolveState {
     std::vector<int> shortcut;      // went to the final check on the iterated residual
     double delta2 = 0.0, inner_tol = 0.0, safety = 0.5;
     int final_rounds = 0, chunk = 4;
+    // residual history at the last chunk boundary, for the length of the next chunk
+    std::vector<double> hist_rr;
+    std::vector<int> hist_it;
+    int next_k = 0;  // predicted iterations to the next stop (0: none yet)
     bool use_graph = false;
     std::chrono::steady_clock::time_point t0;
 
@@ -255,8 +264,13 @@ struct SolveState {
     // choose the right-hand sides of the next inner round and start it; *any
     // is false when no right-hand side needs one
     int plan(bool* any);
-    // iterations the next chunk may run (0: the round must end)
+    // iterations the next chunk may run (0: the round must end): the smaller
+    // of cap() (one chunk, within maxiter) and want() (the prediction)
     int budget() const;
+    int cap() const;
+    int want() const;
+    // extrapolate the iterations to the next stop from the residual history
+    void predict_next();
     // copy the device scalars to the host (the stream is synchronised)
     int read_scalars();
     // after a chunk: reliable updates, breakdowns, iteration limits; *alive is
