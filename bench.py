@@ -618,7 +618,7 @@ def run_batch(args, rank, world, local):
                        "lattices": [list(m.dims) for m in spec], "nrhs": nr,
                        "kappa": [round(m.kappa, 5) for m in spec], "seed": 5005,
                        "l2": "batch links total 0.5 GB FP32: larger than L2"},
-            "clocks": clocks, "gpu_launches": launches,
+            "clocks": clocks, "gpu_launches": launches, "launch_index_range": [l0, l0 + launches],
             # the batch's hopping and vector kernels run inside CUDA graphs,
             # which the per-launch timer does not see: the whole solve's
             # algorithmic bytes over its time
