@@ -20,7 +20,8 @@ pytestmark = pytest.mark.gpu
 SMALL = [((4, 4, 4, 4), (1, 1, 1, -1)),          # Vh = 128: exactly one block
          ((6, 4, 2, 8), (1, np.exp(0.3j), 1, -1)),  # Vh = 192: ragged tail, L = 2, twisted phase
          ((8, 6, 4, 10), (1, 1, 1, -1)),          # Vh = 960: several blocks + tail
-         ((2, 2, 2, 2), (1, 1, 1, -1))]           # L = 2 in every direction
+         ((2, 2, 2, 2), (1, 1, 1, -1)),           # L = 2 in every direction
+         ((6, 2, 2, 6), (-1, 1, np.exp(1.1j), -1))]  # Vh = 72: ragged 32-site tiles and blocks
 
 
 @pytest.fixture(scope="module", params=SMALL, ids=lambda c: "x".join(map(str, c[0])))
@@ -201,5 +202,29 @@ def test_multi_rhs_shapes_match_oracle(monkeypatch, prec, shape):
         bn, xn = b.cpu().numpy(), x.cpu().numpy()
         for r in range(nrhs):
             assert oracle.true_residual(c.U, bn[r], xn[r], c.dims, c.bc, c.kappa) <= 1e-10
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_rhs_beyond_one_launch_chunk(prec):
+    """33 right-hand sides: two launch chunks of the multi-RHS kernel (32 + 1)."""
+    c = Case((4, 2, 4, 6), kappa=0.12, kind="haar", seed=23, bc=(1, 1, 1, -1))
+    try:
+        nrhs = 33
+        psi = c.source(nrhs=nrhs, seed=81)
+        inp = c.to_internal(psi, 1, prec)
+        out = c.g.field(prec, nrhs)
+        wilson.wilson_dslash(c.g.handle, out, inp, 0, 0, PRECS[prec], nrhs)
+        got = c.to_canonical(out, 0, prec, nrhs=nrhs)
+        for r in (0, 31, 32):
+            want = oracle.hop_eo(c.U, c.half(psi, 1, r), c.dims, c.bc, 0)
+            assert rel(c.half(got, 0, r), want) < TOL[prec], r
+        a = torch.zeros(3 * nrhs, dtype=torch.float64, device="cuda")
+        wilson.wl_cdot(c.g.handle, a, out, out, PRECS[prec], nrhs)
+        n = a.cpu().numpy().reshape(nrhs, 3)[:, 2]
+        for r in (0, 32):
+            h = c.half(got, 0, r)
+            assert abs(n[r] - oracle.cdot(h, h).real) < 1e-5 * n[r]
     finally:
         c.close()
