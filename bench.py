@@ -657,6 +657,9 @@ def run_reference(args, rank, world, local):
     from paper_1811_00893_gb300.workloads import by_index
 
     wl = by_index(WORKLOAD_INDEX)
+    if args.dims:  # smaller runs (tests); the default is the workload's own size
+        import dataclasses
+        wl = dataclasses.replace(wl, dims=tuple(int(v) for v in args.dims.split(",")))
     dev = f"cuda:{local}" if torch.cuda.is_available() else "cpu"
     U, b = make_inputs(wl, 0, dev)  # same seeded inputs as the GPU arm
     U_host, b_host = U.cpu().numpy(), b[0].cpu().numpy()

@@ -83,6 +83,9 @@ static const void* pipe_kernel(const HopLaunch& h, int lf)
 // Multi-RHS launch shapes: 1..8 = right-hand-side lanes (warps) of
 // hop_mrhs_kernel; kPipeShape + lanes = the pipelined persistent kernel.
 static const int kPipeShape = 16;
+// Single-RHS reducing launches: block size (grid of resident blocks), or
+// kFullGrid + block size (full grid and a finishing launch).
+static const int kFullGrid = 1000;
 
 // Resident-block grid of the reducing single-RHS hop kernel.
 static int single_grid_cap(const HopLaunch& h, int lf, int block)
@@ -104,8 +107,18 @@ static int launch_shape(const HopLaunch& h, int lf, HopArgs& A, int nrhs, int sh
     A.nparity = h.nparity;
     unsigned gx = (unsigned)(bpp * h.nparity);
     if (!multi) {
-        if (h.dot) gx = std::min(gx, (unsigned)single_grid_cap(h, lf, shape));
-        launch_single(h, lf, A, dim3(gx, 1), shape, s);
+        // shapes above kFullGrid: the reducing kernel over the full grid, one
+        // site per thread, with a finishing launch for the partial sums
+        const bool full = shape > kFullGrid;
+        const int block = full ? shape - kFullGrid : shape;
+        A.partials_only = h.dot && full ? 1 : 0;
+        A.blocks_per_parity = (int)((A.g.Vh + block - 1) / block);
+        gx = (unsigned)((long long)A.blocks_per_parity * h.nparity);
+        if (h.dot && !full) gx = std::min(gx, (unsigned)single_grid_cap(h, lf, block));
+        launch_single(h, lf, A, dim3(gx, 1), block, s);
+        if (A.partials_only)
+            return launch_finish_slots(A.red.partial, (long long)A.red.max_blocks * 3, (int)gx, 1,
+                                       A.dot_out, A.dot_stride, A.active, A.active_stride, s);
     } else if (shape > kPipeShape) {
         const dim3 block(kTile, shape - kPipeShape);
         const size_t smem = 2 * link_site_bytes(h.prec, lf) * kTile + sizeof(double) * 3 * nrhs;
@@ -153,10 +166,11 @@ static int tuned_shape(wl_gauge g, const HopLaunch& h, int lf, HopArgs& A, int n
         return WL_OK;
     }
     *shape = dflt;
-    if (!multi) {  // explicit override of the single-RHS block size (for sweeps)
+    if (!multi) {  // explicit override of the single-RHS shape (for sweeps and tests)
         const char* fb = getenv("WL_HOP_BLOCK");
         const int v = fb ? atoi(fb) : 0;
-        if (v == 64 || v == 128 || v == 256) {
+        const int b = v > kFullGrid ? v - kFullGrid : v;
+        if ((b == 64 || b == 128 || b == 256) && (v < kFullGrid || h.dot)) {
             *shape = v;
             return WL_OK;
         }
@@ -180,6 +194,8 @@ static int tuned_shape(wl_gauge g, const HopLaunch& h, int lf, HopArgs& A, int n
                 if (l <= nrhs) cand.push_back(kPipeShape + l);
     } else {
         cand = {64, 128, 256};
+        if (h.dot)
+            for (int b : {64, 128, 256}) cand.push_back(kFullGrid + b);
     }
     cudaEvent_t e0, e1;
     WL_CUDA(cudaEventCreate(&e0));
@@ -255,6 +271,7 @@ int launch_hop(wl_gauge g, const HopLaunch& h, cudaStream_t s)
     const int lf = (h.prec == WL_F32 || h.prec == WL_F16) && g->links_r12[h.prec][0] && !r12_off ? 1 : 0;
     HopArgs A;
     A.g = g->geo;
+    A.partials_only = 0;
     for (int k = 0; k < 2; ++k) {
         const int p = h.parity0 + (k < h.nparity ? k : 0);
         A.links[k] = lf ? g->links_r12[h.prec][p] : g->links[h.prec][p];

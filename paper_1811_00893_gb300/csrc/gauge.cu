@@ -480,11 +480,11 @@ static int conv_check(wl_gauge g, const void* a, const void* b, int parity, wl_p
 namespace wl {
 
 int field_to_internal(wl_gauge g, void* out, const double* in, int parity, int prec, int nrhs,
-                      cudaStream_t s)
+                      cudaStream_t s, long long out_rs)
 {
     const int block = 128;
     dim3 grid((unsigned)((g->geo.Vh + block - 1) / block), (unsigned)nrhs);
-    const size_t fb = spinor_field_bytes(prec, g->geo.Vh);
+    const size_t fb = out_rs > 0 ? (size_t)out_rs : spinor_field_bytes(prec, g->geo.Vh);
     const long long V = 2 * g->geo.Vh;
     switch (prec) {
         case WL_F64: to_internal_kernel<WL_F64><<<grid, block, 0, s>>>((char*)out, in, g->geo, parity, fb, V); break;
@@ -492,16 +492,16 @@ int field_to_internal(wl_gauge g, void* out, const double* in, int parity, int p
         case WL_F16: to_internal_kernel<WL_F16><<<grid, block, 0, s>>>((char*)out, in, g->geo, parity, fb, V); break;
         default: to_internal_kernel<WL_DF64><<<grid, block, 0, s>>>((char*)out, in, g->geo, parity, fb, V); break;
     }
-    WL_CHECK_LAUNCH((double)nrhs * g->geo.Vh * (192.0 + (double)fb / g->geo.Vh));
+    WL_CHECK_LAUNCH((double)nrhs * g->geo.Vh * (192.0 + (double)spinor_field_bytes(prec, 1)));
     return WL_OK;
 }
 
 int field_to_canonical(wl_gauge g, double* out, const void* in, int parity, int prec, int nrhs,
-                       cudaStream_t s)
+                       cudaStream_t s, long long in_rs)
 {
     const int block = 128;
     dim3 grid((unsigned)((g->geo.Vh + block - 1) / block), (unsigned)nrhs);
-    const size_t fb = spinor_field_bytes(prec, g->geo.Vh);
+    const size_t fb = in_rs > 0 ? (size_t)in_rs : spinor_field_bytes(prec, g->geo.Vh);
     const long long V = 2 * g->geo.Vh;
     switch (prec) {
         case WL_F64: to_canonical_kernel<WL_F64><<<grid, block, 0, s>>>(out, (const char*)in, g->geo, parity, fb, V); break;
@@ -509,7 +509,7 @@ int field_to_canonical(wl_gauge g, double* out, const void* in, int parity, int 
         case WL_F16: to_canonical_kernel<WL_F16><<<grid, block, 0, s>>>(out, (const char*)in, g->geo, parity, fb, V); break;
         default: to_canonical_kernel<WL_DF64><<<grid, block, 0, s>>>(out, (const char*)in, g->geo, parity, fb, V); break;
     }
-    WL_CHECK_LAUNCH((double)nrhs * g->geo.Vh * (192.0 + (double)fb / g->geo.Vh));
+    WL_CHECK_LAUNCH((double)nrhs * g->geo.Vh * (192.0 + (double)spinor_field_bytes(prec, 1)));
     return WL_OK;
 }
 

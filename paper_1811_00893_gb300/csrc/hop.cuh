@@ -510,6 +510,10 @@ struct HopArgs {
     const int* active;
     int active_stride;
     RedScratch red;
+    // reducing single-RHS kernel: 0 = grid of resident blocks, the last block
+    // adds the partials; 1 = one site per thread, every block leaves its
+    // partial and a finishing launch adds them (no grid-stride loop)
+    int partials_only;
 };
 
 // Clover modes of the epilogue (Eq. 2's site-diagonal A = 1 + F or its
@@ -549,7 +553,28 @@ __device__ __forceinline__ void epilogue_ptrs(cx<typename Prec<P>::real> (&acc)[
     }
     if (CL == kClOut) clover_mul<P>(acc, cl, Vh, i);
     store_spinor<P>(out, Vh, i, acc);
-    if (DOT) {
+    if constexpr (DOT && P == WL_DF64) {
+        // The double-float kernels produce outer residuals: the residual itself
+        // needs the 48-bit arithmetic (it is a small difference of large
+        // terms), its norm and dots only a few digits.  Summed from the high
+        // words in FP32: ~2^-24 relative, at a tenth of the double-float cost.
+        float cr = 0.f, ci = 0.f, nn = 0.f;
+        if (w) {
+            cx<T> ww[12];
+            load_spinor<P>(ww, w, Vh, i);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                cr = fmaf(ww[c].re.hi, acc[c].re.hi, fmaf(ww[c].im.hi, acc[c].im.hi, cr));
+                ci = fmaf(ww[c].re.hi, acc[c].im.hi, fmaf(-ww[c].im.hi, acc[c].re.hi, ci));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 12; ++c)
+            nn = fmaf(acc[c].re.hi, acc[c].re.hi, fmaf(acc[c].im.hi, acc[c].im.hi, nn));
+        part[0] = T(cr);
+        part[1] = T(ci);
+        part[2] = T(nn);
+    } else if constexpr (DOT) {
         T cr = 0, ci = 0, nn = 0;
         if (w) {
             cx<T> ww[12];

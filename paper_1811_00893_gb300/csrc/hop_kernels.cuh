@@ -92,6 +92,12 @@ __global__ void __launch_bounds__(256, (MinBlocks<P, DOT>::value)) hop_kernel(co
         double part[3] = {(double)wp[0], (double)wp[1], (double)wp[2]};
         __shared__ double sh[3 * 32];
         block_sum_warps<3>(part, sh);
+        if (A.partials_only) {
+            if (threadIdx.x == 0)
+                for (int k = 0; k < 3; ++k)
+                    A.red.partial[((long long)rhs * A.red.max_blocks + blockIdx.x) * 3 + k] = part[k];
+            return;
+        }
         double tot[3];
         if (grid_sum<3>(part, tot, A.red, rhs, gridDim.x, blockIdx.x, sh)) {
             double* o = A.dot_out + (long long)rhs * A.dot_stride;

@@ -141,10 +141,12 @@ int launch_accum_hi(wl_gauge g, int phi, void* xhi, int plo, const void* xlo, in
 bool is_capturing(cudaStream_t s);
 
 // Layout conversion for any storage precision (including the internal df64).
+// out_rs / in_rs: bytes between right-hand sides of the internal field (0:
+// contiguous half fields).
 int field_to_internal(wl_gauge g, void* out, const double* in, int parity, int prec, int nrhs,
-                      cudaStream_t s);
+                      cudaStream_t s, long long out_rs = 0);
 int field_to_canonical(wl_gauge g, double* out, const void* in, int parity, int prec, int nrhs,
-                       cudaStream_t s);
+                       cudaStream_t s, long long in_rs = 0);
 
 // Blocks of `kernel` (block threads, dynamic smem bytes) that fit on the whole
 // GPU at once: the grid of a grid-stride kernel whose reduction should have

@@ -741,18 +741,12 @@ int SolveState::begin(wl_gauge g_, double* x, const double* b, int nrhs_, const 
         }
     }
     const size_t hb64 = w->hb64;
-    // b -> internal FP64 (even | odd per rhs); one conversion per rhs and parity
-    for (int r = 0; r < nrhs; ++r) {
-        char* dst = (char*)w->b64 + r * 2 * hb64;
-        const double* src = bd + (size_t)r * V * 24;
-        WL_TRY(field_to_internal(g, dst, src, 0, WL_F64, 1, s));
-        WL_TRY(field_to_internal(g, dst + hb64, src, 1, WL_F64, 1, s));
-        if (prm->use_x0) {
-            char* xdst = (char*)w->xhi + r * 2 * hb64;
-            const double* xs = xd + (size_t)r * V * 24;
-            WL_TRY(field_to_internal(g, xdst, xs, 0, w->outer, 1, s));
-            WL_TRY(field_to_internal(g, xdst + hb64, xs, 1, w->outer, 1, s));
-        }
+    // b -> internal FP64 (even | odd per rhs): one conversion per parity for all rhs
+    WL_TRY(field_to_internal(g, w->b64, bd, 0, WL_F64, nrhs, s, 2 * (long long)hb64));
+    WL_TRY(field_to_internal(g, (char*)w->b64 + hb64, bd, 1, WL_F64, nrhs, s, 2 * (long long)hb64));
+    if (prm->use_x0) {
+        WL_TRY(field_to_internal(g, w->xhi, xd, 0, w->outer, nrhs, s, 2 * (long long)hb64));
+        WL_TRY(field_to_internal(g, (char*)w->xhi + hb64, xd, 1, w->outer, nrhs, s, 2 * (long long)hb64));
     }
     if (!prm->use_x0) WL_CUDA(cudaMemsetAsync(w->xhi, 0, 2 * hb64 * nrhs, s));
     // ||b||^2 over the full lattice
@@ -1082,12 +1076,8 @@ int SolveState::end(wl_solve_info* info)
 {
     const size_t hb64 = w->hb64;
     const long long V = 2 * g->geo.Vh;
-    for (int r = 0; r < nrhs; ++r) {
-        const char* src = (const char*)w->x64 + r * 2 * hb64;
-        double* dst = xd + (size_t)r * V * 24;
-        WL_TRY(field_to_canonical(g, dst, src, 0, WL_F64, 1, s));
-        WL_TRY(field_to_canonical(g, dst, src + hb64, 1, WL_F64, 1, s));
-    }
+    WL_TRY(field_to_canonical(g, xd, w->x64, 0, WL_F64, nrhs, s, 2 * (long long)hb64));
+    WL_TRY(field_to_canonical(g, xd, (const char*)w->x64 + hb64, 1, WL_F64, nrhs, s, 2 * (long long)hb64));
     if (host_x) WL_CUDA(cudaMemcpyAsync(x_user, xd, canon, cudaMemcpyDeviceToHost, s));
     WL_CUDA(cudaStreamSynchronize(s));
     const double secs =

@@ -228,3 +228,23 @@ def test_rhs_beyond_one_launch_chunk(prec):
             assert abs(n[r] - oracle.cdot(h, h).real) < 1e-5 * n[r]
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("shape", [64, 256, 1064, 1128])
+def test_reducing_hop_shapes_in_solve(monkeypatch, shape):
+    """Both forms of the reducing single-RHS hop (grid of resident blocks with
+    a last-block sum; full grid with a finishing launch, shapes 1000 + block)
+    drive a solve to the true residual."""
+    monkeypatch.setenv("WL_HOP_BLOCK", str(shape))
+    c = Case((6, 2, 2, 6), kappa=0.124, kind="haar", seed=29, bc=(1, 1, 1, -1))
+    try:
+        b = c.source(nrhs=1, seed=91)
+        for inner in (wilson.WL_F32, wilson.WL_F64):
+            x = torch.zeros_like(b)
+            rc, info = wilson.wilson_solve(c.g.handle, x, b, 1,
+                                           wilson.solve_params(tol=1e-10, eo=True, inner=inner))
+            tr = oracle.true_residual(c.U, b[0].cpu().numpy(), x[0].cpu().numpy(), c.dims, c.bc,
+                                      c.kappa)
+            assert tr <= 1e-10 and abs(info[0]["true_resid"] - tr) <= 0.05 * tr + 1e-15, (shape, inner)
+    finally:
+        c.close()
