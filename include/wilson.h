@@ -236,10 +236,16 @@ typedef struct {
 int wilson_solve(wl_gauge g, double* x, const double* b, int nrhs, const wl_solve_params* p,
                  wl_solve_info* info, void* stream);
 
-/* Solve nlat independent systems of different lattices together: gauge
- * object gs[l] with nrhs[l] right-hand sides x[l], b[l] (device, canonical).
- * Hopping and vector kernels run as single persistent launches over all
- * lattices.  info receives sum(nrhs) entries, lattice by lattice. */
+/* Solve nlat independent systems of different lattices together (the
+ * batched form of wilson_solve): gauge object gs[l] with nrhs[l] right-hand
+ * sides x[l], b[l] (device memory, canonical).  Each inner BiCGStab operator
+ * is one persistent hopping launch over 32-site tiles of all lattices (tiles
+ * of lattices whose systems have all stopped are skipped), each vector update
+ * one launch over all systems; the outer work runs per lattice.  Limits:
+ * 1 <= nlat <= 64, 1 <= nrhs[l] <= 32, even-odd systems only (p->eo = 1),
+ * each gauge object at most once; WL_ERR_ARG otherwise.  A gauge object
+ * with a clover term contributes D_clov.  info receives sum(nrhs) entries,
+ * lattice by lattice.  Synchronises the stream. */
 int wilson_solve_batch(int nlat, const wl_gauge* gs, double* const* x, const double* const* b,
                        const int* nrhs, const wl_solve_params* p, wl_solve_info* info,
                        void* stream);
@@ -253,7 +259,9 @@ long long wl_launch_count(void);
 
 /* Algorithmic bytes of those launches: each kernel counts the fields it must
  * read and write once (links once per hopping launch for all right-hand
- * sides, every spinor operand once), not the traffic the hardware saw. */
+ * sides, every spinor operand once), not the traffic the hardware saw.
+ * Iterations a solver chunk launched after every right-hand side had
+ * stopped (whose kernels exit at once) are taken out again. */
 double wl_algorithmic_bytes(void);
 
 /* Per-launch CUDA-event timing of the hopping kernels launched by this gauge
@@ -261,7 +269,9 @@ double wl_algorithmic_bytes(void);
  * enable = 1 clears and starts recording, enable = 0 stops.  wl_timing_read
  * returns, for hopping launches of precision `prec` (-1: all), the summed
  * kernel time in ms, the number of timed launches and their summed
- * algorithmic bytes.  It waits for the recorded events. */
+ * algorithmic bytes, leaving out launches that found no work (a solver
+ * chunk's iterations after every right-hand side had stopped).  It waits for
+ * the recorded events. */
 int wl_timing(wl_gauge g, int enable);
 int wl_timing_read(wl_gauge g, int prec, double* ms, long long* launches, double* bytes);
 

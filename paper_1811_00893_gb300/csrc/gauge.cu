@@ -28,6 +28,22 @@ Geom make_geom(const int* dims)
     g.sy = g.Lxh;
     g.sz = g.sy * dims[1];
     g.st = g.sz * dims[2];
+    // Round-up reciprocals (Granlund-Montgomery): with l = ceil(log2 d) and
+    // m = floor(2^(31+l) / d) + 1 < 2^32, floor(n m / 2^(31+l)) = n / d
+    // exactly for 0 <= n < 2^31, since m d - 2^(31+l) <= d <= 2^l.
+    const int div[3] = {g.Lxh, dims[1], dims[2]};
+    for (int k = 0; k < 3; ++k) {
+        const unsigned long long d = (unsigned long long)div[k];
+        if (d <= 1) {
+            g.dm[k] = 0;
+            g.ds[k] = 0;
+            continue;
+        }
+        int l = 0;
+        while ((1ull << l) < d) ++l;
+        g.dm[k] = (unsigned)((1ull << (31 + l)) / d + 1);
+        g.ds[k] = l - 1;
+    }
     return g;
 }
 

@@ -175,16 +175,30 @@ __device__ __forceinline__ void load_link_row<WL_DF64>(cx<df64> (&w)[3], const v
     }
 }
 
+// n / (Lxh, Ly, Lz)[k] without an integer divide (Geom::dm, ds);
+// WL_FAST_DIV=0 builds the plain division instead (for comparisons)
+#ifndef WL_FAST_DIV
+#define WL_FAST_DIV 1
+#endif
+__device__ __forceinline__ int geo_div(const Geom& g, int k, int n)
+{
+#if WL_FAST_DIV
+    return g.dm[k] ? (int)(__umulhi((unsigned)n, g.dm[k]) >> g.ds[k]) : n;
+#else
+    return n / (k == 0 ? g.Lxh : g.L[k]);
+#endif
+}
+
 // Half indices of the eight neighbours (order +x, -x, +y, -y, +z, -z, +t, -t)
 // of output site i on parity p, with periodic wrap-around.
 __device__ __forceinline__ void neighbours(const Geom& g, int p, int i, int (&nb)[8])
 {
-    const int xh = i % g.Lxh;
-    int r = i / g.Lxh;
-    const int y = r % g.L[1];
-    r /= g.L[1];
-    const int z = r % g.L[2];
-    const int t = r / g.L[2];
+    const int r0 = geo_div(g, 0, i);  // (y, z, t) row
+    const int xh = i - r0 * g.Lxh;
+    const int r1 = geo_div(g, 1, r0);
+    const int y = r0 - r1 * g.L[1];
+    const int t = geo_div(g, 2, r1);
+    const int z = r1 - t * g.L[2];
     const int x = 2 * xh + ((p + y + z + t) & 1);
     const int row = i - xh;
     const int sy = (int)g.sy, sz = (int)g.sz, st = (int)g.st;
@@ -205,12 +219,12 @@ __device__ __forceinline__ void neighbours(const Geom& g, int p, int i, int (&nb
 __device__ __forceinline__ void neighbours(const Geom& g, int p, int i, int (&nb)[8], unsigned& cross)
 {
     neighbours(g, p, i, nb);
-    const int xh = i % g.Lxh;
-    int r = i / g.Lxh;
-    const int y = r % g.L[1];
-    r /= g.L[1];
-    const int z = r % g.L[2];
-    const int t = r / g.L[2];
+    const int r0 = geo_div(g, 0, i);
+    const int xh = i - r0 * g.Lxh;
+    const int r1 = geo_div(g, 1, r0);
+    const int y = r0 - r1 * g.L[1];
+    const int t = geo_div(g, 2, r1);
+    const int z = r1 - t * g.L[2];
     const int x = 2 * xh + ((p + y + z + t) & 1);
     const int c[4] = {x, y, z, t};
     cross = 0;
@@ -523,6 +537,47 @@ struct HopArgs {
 //   CL = 2: out = C (x1 + b1 x2 + a acc)        (A^-1 H in)
 enum { kClNone = 0, kClX2 = 1, kClOut = 2 };
 
+// (w, out) and ||out||^2 of one site into part.  The double-float kernels
+// produce outer residuals: the residual itself needs the 48-bit arithmetic (a
+// small difference of large terms), its norm and dots only a few digits, so
+// they are summed from the high words in FP32 (~2^-24 relative, a tenth of
+// the double-float cost).
+template <int P>
+__device__ __forceinline__ void site_dots(const cx<typename Prec<P>::real> (&acc)[12],
+                                          const cx<typename Prec<P>::real>* ww,
+                                          typename Prec<P>::real (&part)[3])
+{
+    using T = typename Prec<P>::real;
+    if constexpr (P == WL_DF64) {
+        float cr = 0.f, ci = 0.f, nn = 0.f;
+        if (ww)
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                cr = fmaf(ww[c].re.hi, acc[c].re.hi, fmaf(ww[c].im.hi, acc[c].im.hi, cr));
+                ci = fmaf(ww[c].re.hi, acc[c].im.hi, fmaf(-ww[c].im.hi, acc[c].re.hi, ci));
+            }
+#pragma unroll
+        for (int c = 0; c < 12; ++c)
+            nn = fmaf(acc[c].re.hi, acc[c].re.hi, fmaf(acc[c].im.hi, acc[c].im.hi, nn));
+        part[0] = T(cr);
+        part[1] = T(ci);
+        part[2] = T(nn);
+    } else {
+        T cr = 0, ci = 0, nn = 0;
+        if (ww)
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                cr = fma(ww[c].re, acc[c].re, fma(ww[c].im, acc[c].im, cr));
+                ci = fma(ww[c].re, acc[c].im, fma(-ww[c].im, acc[c].re, ci));
+            }
+#pragma unroll
+        for (int c = 0; c < 12; ++c) nn = fma(acc[c].re, acc[c].re, fma(acc[c].im, acc[c].im, nn));
+        part[0] = cr;
+        part[1] = ci;
+        part[2] = nn;
+    }
+}
+
 // out = x1 + b1 x2 + a acc at site i (x1, x2 optional; clover per CL); with
 // DOT the thread's contributions to (w, out) (w optional) and ||out||^2 go to
 // part.
@@ -553,43 +608,14 @@ __device__ __forceinline__ void epilogue_ptrs(cx<typename Prec<P>::real> (&acc)[
     }
     if (CL == kClOut) clover_mul<P>(acc, cl, Vh, i);
     store_spinor<P>(out, Vh, i, acc);
-    if constexpr (DOT && P == WL_DF64) {
-        // The double-float kernels produce outer residuals: the residual itself
-        // needs the 48-bit arithmetic (it is a small difference of large
-        // terms), its norm and dots only a few digits.  Summed from the high
-        // words in FP32: ~2^-24 relative, at a tenth of the double-float cost.
-        float cr = 0.f, ci = 0.f, nn = 0.f;
+    if (DOT) {
         if (w) {
             cx<T> ww[12];
             load_spinor<P>(ww, w, Vh, i);
-#pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                cr = fmaf(ww[c].re.hi, acc[c].re.hi, fmaf(ww[c].im.hi, acc[c].im.hi, cr));
-                ci = fmaf(ww[c].re.hi, acc[c].im.hi, fmaf(-ww[c].im.hi, acc[c].re.hi, ci));
-            }
+            site_dots<P>(acc, ww, part);
+        } else {
+            site_dots<P>(acc, nullptr, part);
         }
-#pragma unroll
-        for (int c = 0; c < 12; ++c)
-            nn = fmaf(acc[c].re.hi, acc[c].re.hi, fmaf(acc[c].im.hi, acc[c].im.hi, nn));
-        part[0] = T(cr);
-        part[1] = T(ci);
-        part[2] = T(nn);
-    } else if constexpr (DOT) {
-        T cr = 0, ci = 0, nn = 0;
-        if (w) {
-            cx<T> ww[12];
-            load_spinor<P>(ww, w, Vh, i);
-#pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                cr = fma(ww[c].re, acc[c].re, fma(ww[c].im, acc[c].im, cr));
-                ci = fma(ww[c].re, acc[c].im, fma(-ww[c].im, acc[c].re, ci));
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < 12; ++c) nn = fma(acc[c].re, acc[c].re, fma(acc[c].im, acc[c].im, nn));
-        part[0] = cr;
-        part[1] = ci;
-        part[2] = nn;
     }
 }
 

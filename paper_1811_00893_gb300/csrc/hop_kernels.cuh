@@ -47,11 +47,33 @@ struct MinBlocks {
     static constexpr int value = DOT && base > 2 ? 2 : base;  // the reducing loop needs more
 };
 
+// Ask L2 for the site's epilogue operands (x1, x2, w) before the stencil
+// starts, so that their loads after the eight hops do not wait on HBM.  A
+// prefetch holds no register.  WL_PREFETCH_EPILOGUE=0 builds without it.
+#ifndef WL_PREFETCH_EPILOGUE
+#define WL_PREFETCH_EPILOGUE 1
+#endif
+template <int P>
+__device__ __forceinline__ void prefetch_spinor_l2(const char* base, long long Vh, long long i)
+{
+    constexpr int planes = (P == WL_F32) ? 6 : (P == WL_F16) ? 3 : 12;  // 16-byte planes
+#pragma unroll
+    for (int k = 0; k < planes; ++k)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (k * Vh + i) * 16));
+    if (P == WL_F16) asm volatile("prefetch.global.L2 [%0];" ::"l"(base + 3 * Vh * 16 + i * 4));
+}
+
 template <int P, bool DAG, bool DOT, int CL, int LF>
 __device__ __forceinline__ void hop_kernel_site(const HopArgs& A, int rhs, int pidx, int i,
                                                 typename Prec<P>::real (&part)[3])
 {
     using T = typename Prec<P>::real;
+    if (WL_PREFETCH_EPILOGUE) {
+        if (A.x1[pidx]) prefetch_spinor_l2<P>(A.x1[pidx] + rhs * A.rs_x1, A.g.Vh, i);
+        if (A.x2[pidx]) prefetch_spinor_l2<P>(A.x2[pidx] + rhs * A.rs_x2, A.g.Vh, i);
+        if (DOT && A.w[pidx] && A.w[pidx] != A.x1[pidx])
+            prefetch_spinor_l2<P>(A.w[pidx] + rhs * A.rs_w, A.g.Vh, i);
+    }
     cx<T> acc[12];
     int nb[8];
     unsigned cross = 0;

@@ -17,6 +17,10 @@ struct Geom {
     int Lxh;       // Lx / 2
     long long Vh;  // half volume
     long long sy, sz, st;  // half-index strides of y, z, t
+    // division by Lxh, Ly, Lz by multiply-high and shift (set by make_geom):
+    // n / d = umulhi(n, dm) >> ds for 0 <= n < 2^31 (dm = 0: d = 1)
+    unsigned dm[3];
+    int ds[3];
 };
 
 // Per-launch event timing of hopping kernels (see wl_timing).
