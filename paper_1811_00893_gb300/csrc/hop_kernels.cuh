@@ -49,7 +49,9 @@ struct MinBlocks {
 
 // Ask L2 for the site's epilogue operands (x1, x2, w) before the stencil
 // starts, so that their loads after the eight hops do not wait on HBM.  A
-// prefetch holds no register.  WL_PREFETCH_EPILOGUE=0 builds without it.
+// prefetch holds no register.  Measured: FP16 solve 149.8 -> 148.5 ms, but
+// the FP32 hop 141 -> 151 us (its register budget tips into spills), so only
+// the FP16 kernels prefetch.  WL_PREFETCH_EPILOGUE=0 builds without it.
 #ifndef WL_PREFETCH_EPILOGUE
 #define WL_PREFETCH_EPILOGUE 1
 #endif
@@ -68,7 +70,7 @@ __device__ __forceinline__ void hop_kernel_site(const HopArgs& A, int rhs, int p
                                                 typename Prec<P>::real (&part)[3])
 {
     using T = typename Prec<P>::real;
-    if (WL_PREFETCH_EPILOGUE) {
+    if (WL_PREFETCH_EPILOGUE && P == WL_F16) {
         if (A.x1[pidx]) prefetch_spinor_l2<P>(A.x1[pidx] + rhs * A.rs_x1, A.g.Vh, i);
         if (A.x2[pidx]) prefetch_spinor_l2<P>(A.x2[pidx] + rhs * A.rs_x2, A.g.Vh, i);
         if (DOT && A.w[pidx] && A.w[pidx] != A.x1[pidx])
