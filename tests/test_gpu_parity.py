@@ -179,10 +179,11 @@ def test_cdot_matches_oracle(case, prec):
 def test_multi_rhs_shapes_match_oracle(monkeypatch, prec, shape):
     """Every multi-RHS launch shape the autotuner may pick (warps per block of
     the staged kernel; 16 + warps for the pipelined persistent kernel) gives
-    the oracle's hopping term and reductions, on a lattice with a ragged last
-    tile."""
+    the oracle's hopping term and reductions, on a lattice whose last 32-site
+    tile is half empty (Vh = 144).  The solve also runs its FP64 and
+    double-float multi-RHS launches in the forced shape."""
     monkeypatch.setenv("WL_MRHS_SHAPE", str(shape))
-    c = Case((6, 4, 2, 8), kappa=0.124, kind="haar", seed=9, bc=(1, np.exp(0.3j), 1, -1))
+    c = Case((6, 4, 2, 6), kappa=0.124, kind="haar", seed=9, bc=(1, np.exp(0.3j), 1, -1))
     try:
         nrhs = 5
         psi = c.source(nrhs=nrhs, seed=71)
