@@ -88,6 +88,8 @@ __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b)
 template <typename T>
 __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return {s * a.re, s * a.im}; }
 template <typename T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a) { return {-a.re, -a.im}; }
+template <typename T>
 __device__ __forceinline__ cx<T> conj(cx<T> a) { return {a.re, -a.im}; }
 // i * a
 template <typename T>

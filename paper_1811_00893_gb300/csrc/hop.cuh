@@ -332,6 +332,50 @@ __device__ __forceinline__ void load_spinor_ro_f16_unscaled(cx<float> (&v)[12], 
     }
 }
 
+// FP16 half h plus the FP32 value c, rounded once in FP32: the result of
+// converting h (exactly) and adding in FP32, as one mixed-precision add
+// (sm_100 and later) instead of a conversion and an add.
+__device__ __forceinline__ float add_f16_f32(unsigned short h, float c)
+{
+    float d;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(h), "f"(c));
+    return d;
+}
+
+// The projection above on an FP16 spinor given as 12 words (complex entry
+// spin * 3 + colour, real part in the low half): spins 2 and 3 are converted
+// to FP32 and enter the mixed adds with spins 0 and 1, which stay FP16.  The
+// sums are the FP32 sums of the converted values, rounded once.
+#ifndef WL_F16_MIXED_ADD
+#define WL_F16_MIXED_ADD 1
+#endif
+template <int MU, int S>
+__device__ __forceinline__ void project_f16(cx<float> (&h0)[3], cx<float> (&h1)[3], const unsigned (&w)[12])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 f2 = h2f(w[6 + c]), f3 = h2f(w[9 + c]);
+        const cx<float> p2 = {f2.x, f2.y}, p3 = {f3.x, f3.y};
+        cx<float> b0, b1;  // the terms added to spins 0 and 1
+        if constexpr (MU == 0) {
+            b0 = S > 0 ? mul_i(p3) : -mul_i(p3);
+            b1 = S > 0 ? mul_i(p2) : -mul_i(p2);
+        } else if constexpr (MU == 1) {
+            b0 = S > 0 ? -p3 : p3;
+            b1 = S > 0 ? p2 : -p2;
+        } else if constexpr (MU == 2) {
+            b0 = S > 0 ? mul_i(p2) : -mul_i(p2);
+            b1 = S > 0 ? -mul_i(p3) : mul_i(p3);
+        } else {
+            b0 = S > 0 ? p2 : -p2;
+            b1 = S > 0 ? p3 : -p3;
+        }
+        const unsigned p0 = w[c], p1 = w[3 + c];
+        h0[c] = {add_f16_f32((unsigned short)(p0 & 0xffffu), b0.re), add_f16_f32((unsigned short)(p0 >> 16), b0.im)};
+        h1[c] = {add_f16_f32((unsigned short)(p1 & 0xffffu), b1.re), add_f16_f32((unsigned short)(p1 >> 16), b1.im)};
+    }
+}
+
 // the projected half spinor of the neighbour spinor at index nb
 template <int P, int MU, int S>
 __device__ __forceinline__ void load_project(cx<typename Prec<P>::real> (&h0)[3],
@@ -342,8 +386,26 @@ __device__ __forceinline__ void load_project(cx<typename Prec<P>::real> (&h0)[3]
     cx<T> q[12];
     if constexpr (P == WL_F16) {
         float nrm;
+#if WL_F16_MIXED_ADD
+        (void)q;
+        unsigned w[12];
+        {
+            const uint4* p = (const uint4*)in;
+            nrm = __ldg((const float*)(p + 3 * Vh) + nb);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const uint4 t = __ldg(p + k * Vh + nb);
+                w[4 * k + 0] = t.x;
+                w[4 * k + 1] = t.y;
+                w[4 * k + 2] = t.z;
+                w[4 * k + 3] = t.w;
+            }
+        }
+        project_f16<MU, S>(h0, h1, w);
+#else
         load_spinor_ro_f16_unscaled(q, nrm, in, Vh, nb);
         project<MU, S>(h0, h1, q);
+#endif
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             h0[c] = nrm * h0[c];
