@@ -588,6 +588,29 @@ def run_batch(args, rank, world, local):
         work += Vh * (max(its) * link_part + sum(its) * (per_iter - link_part))
     total_bytes, ms = aggregate(work * args.steps, ms_local, world, device=dev)
 
+    # ---------------- e2e: each step copies every b from pinned host memory
+    # to the device, solves the batch and copies every x back (the batch call
+    # takes device buffers, so the copies are the caller's)
+    bs_h = [t.cpu().pin_memory() for t in bs]
+    xs_h = [torch.zeros_like(t).pin_memory() for t in bs_h]
+
+    def e2e_step():
+        for th, td in zip(bs_h, bs):
+            td.copy_(th, non_blocking=True)
+        wilson.wilson_solve_batch(hs, xs, bs, nr, p)
+        for th, td in zip(xs_h, xs):
+            th.copy_(td, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_step()
+    e2e_steps = max(1, args.steps // 2)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    _, e2e_ms = aggregate(0.0, (time.perf_counter() - t0) * 1e3 / e2e_steps, world, device=dev)
+    nbytes_io = sum(t.numel() * t.element_size() for t in bs)
+
     def timed(fn):
         fn()
         torch.cuda.synchronize()
@@ -618,7 +641,13 @@ def run_batch(args, rank, world, local):
                        "lattices": [list(m.dims) for m in spec], "nrhs": nr,
                        "kappa": [round(m.kappa, 5) for m in spec], "seed": 5005,
                        "l2": "batch links total 0.5 GB FP32: larger than L2"},
-            "clocks": clocks, "gpu_launches": launches, "launch_index_range": [l0, l0 + launches],
+            "clocks": clocks,
+            "e2e": {"value": total_bytes / args.steps / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": nbytes_io, "d2h_bytes_per_step": nbytes_io,
+                    "ms_per_step": e2e_ms,
+                    "timer": "wall clock around the host-to-device copies of every b, "
+                             "wilson_solve_batch and the copies of every x back to pinned host"},
+            "gpu_launches": launches, "launch_index_range": [l0, l0 + launches],
             # the batch's hopping and vector kernels run inside CUDA graphs,
             # which the per-launch timer does not see: the whole solve's
             # algorithmic bytes over its time

@@ -250,6 +250,15 @@ int wilson_solve_batch(int nlat, const wl_gauge* gs, double* const* x, const dou
                        const int* nrhs, const wl_solve_params* p, wl_solve_info* info,
                        void* stream);
 
+/* Encoding of the 16-bit words of WL_F16 spinors in this build.  Both forms
+ * store each value divided by its site's max |component| (the FP32 norm kept
+ * beside the site), so that it lies in [-1, 1]:
+ *   0  IEEE binary16, round to nearest even (the default build);
+ *   1  int16 fixed point: round(32767 v), stored biased by 32768 (a build
+ *      with -DWL_SPINOR16_FIXED=1).
+ * Links and clover matrices of WL_F16 are binary16 in both builds. */
+int wl_spinor16_format(void);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* wl_last_error(void);
 

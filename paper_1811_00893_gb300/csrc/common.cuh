@@ -239,16 +239,49 @@ __device__ __forceinline__ unsigned f2h(float a, float b)
     return *reinterpret_cast<unsigned*>(&h);
 }
 
+// Codec of the 16-bit spinor words (two values per word, real part in the
+// low half), applied to the value divided by the site's max |component|, so
+// that it lies in [-1, 1].  Default: IEEE binary16 (2^-11 relative
+// rounding).  WL_SPINOR16_FIXED=1 builds int16 fixed point instead: the value
+// times 32767, rounded to nearest, which is 2^-16 of the site scale absolute.
+// It is stored biased by 32768 so that decoding is a byte permute into the
+// mantissa of 2^23 and one subtraction, both exact.  kSpin16Unit is the value
+// of one decoded unit; the kernels fold it into the site norm.
+#ifndef WL_SPINOR16_FIXED
+#define WL_SPINOR16_FIXED 0
+#endif
+constexpr float kSpin16Unit = WL_SPINOR16_FIXED ? 1.0f / 32767.0f : 1.0f;
+__device__ __forceinline__ float2 s16_dec(unsigned u)
+{
+#if WL_SPINOR16_FIXED
+    const float bias = 8421376.0f;  // 2^23 + 32768
+    return make_float2(__uint_as_float(__byte_perm(u, 0x4B000000u, 0x7610)) - bias,
+                       __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7632)) - bias);
+#else
+    return h2f(u);
+#endif
+}
+__device__ __forceinline__ unsigned s16_enc(float a, float b)
+{
+#if WL_SPINOR16_FIXED
+    const int qa = min(32767, max(-32767, __float2int_rn(a * 32767.0f)));
+    const int qb = min(32767, max(-32767, __float2int_rn(b * 32767.0f)));
+    return (unsigned)(qa + 32768) | ((unsigned)(qb + 32768) << 16);
+#else
+    return f2h(a, b);
+#endif
+}
+
 template <>
 __device__ __forceinline__ void load_spinor<WL_F16>(cx<float> (&v)[12], const void* base,
                                                     long long Vh, long long i)
 {
     const uint4* p = (const uint4*)base;
-    const float nrm = ((const float*)(p + 3 * Vh))[i];
+    const float nrm = ((const float*)(p + 3 * Vh))[i] * kSpin16Unit;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         uint4 t = p[k * Vh + i];
-        float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), d = h2f(t.w);
+        float2 a = s16_dec(t.x), b = s16_dec(t.y), c = s16_dec(t.z), d = s16_dec(t.w);
         v[4 * k + 0] = {a.x * nrm, a.y * nrm};
         v[4 * k + 1] = {b.x * nrm, b.y * nrm};
         v[4 * k + 2] = {c.x * nrm, c.y * nrm};
@@ -267,10 +300,10 @@ __device__ __forceinline__ void store_spinor<WL_F16>(void* base, long long Vh, l
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         uint4 t;
-        t.x = f2h(v[4 * k + 0].re * s, v[4 * k + 0].im * s);
-        t.y = f2h(v[4 * k + 1].re * s, v[4 * k + 1].im * s);
-        t.z = f2h(v[4 * k + 2].re * s, v[4 * k + 2].im * s);
-        t.w = f2h(v[4 * k + 3].re * s, v[4 * k + 3].im * s);
+        t.x = s16_enc(v[4 * k + 0].re * s, v[4 * k + 0].im * s);
+        t.y = s16_enc(v[4 * k + 1].re * s, v[4 * k + 1].im * s);
+        t.z = s16_enc(v[4 * k + 2].re * s, v[4 * k + 2].im * s);
+        t.w = s16_enc(v[4 * k + 3].re * s, v[4 * k + 3].im * s);
         p[k * Vh + i] = t;
     }
     ((float*)(p + 3 * Vh))[i] = m;
@@ -311,11 +344,11 @@ __device__ __forceinline__ void load_spinor_ro<WL_F16>(cx<float> (&v)[12], const
                                                        long long Vh, long long i)
 {
     const uint4* p = (const uint4*)base;
-    const float nrm = __ldg((const float*)(p + 3 * Vh) + i);
+    const float nrm = __ldg((const float*)(p + 3 * Vh) + i) * kSpin16Unit;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         uint4 t = __ldg(p + k * Vh + i);
-        float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), d = h2f(t.w);
+        float2 a = s16_dec(t.x), b = s16_dec(t.y), c = s16_dec(t.z), d = s16_dec(t.w);
         v[4 * k + 0] = {a.x * nrm, a.y * nrm};
         v[4 * k + 1] = {b.x * nrm, b.y * nrm};
         v[4 * k + 2] = {c.x * nrm, c.y * nrm};

@@ -549,6 +549,8 @@ extern "C" int wl_field_to_canonical(wl_gauge g, double* out, const void* in, in
 
 extern "C" const char* wl_last_error(void) { return wl::t_last_error.c_str(); }
 
+extern "C" int wl_spinor16_format(void) { return WL_SPINOR16_FIXED ? 1 : 0; }
+
 extern "C" long long wl_launch_count(void) { return wl::g_launches.load(); }
 
 extern "C" double wl_algorithmic_bytes(void) { return (double)wl::g_bytes.load(); }

@@ -320,11 +320,11 @@ __device__ __forceinline__ void load_spinor_ro_f16_unscaled(cx<float> (&v)[12], 
                                                            const void* base, long long Vh, long long i)
 {
     const uint4* p = (const uint4*)base;
-    nrm = __ldg((const float*)(p + 3 * Vh) + i);
+    nrm = __ldg((const float*)(p + 3 * Vh) + i) * kSpin16Unit;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const uint4 t = __ldg(p + k * Vh + i);
-        const float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), d = h2f(t.w);
+        const float2 a = s16_dec(t.x), b = s16_dec(t.y), c = s16_dec(t.z), d = s16_dec(t.w);
         v[4 * k + 0] = {a.x, a.y};
         v[4 * k + 1] = {b.x, b.y};
         v[4 * k + 2] = {c.x, c.y};
@@ -347,7 +347,7 @@ __device__ __forceinline__ float add_f16_f32(unsigned short h, float c)
 // to FP32 and enter the mixed adds with spins 0 and 1, which stay FP16.  The
 // sums are the FP32 sums of the converted values, rounded once.
 #ifndef WL_F16_MIXED_ADD
-#define WL_F16_MIXED_ADD 1
+#define WL_F16_MIXED_ADD (!WL_SPINOR16_FIXED)
 #endif
 template <int MU, int S>
 __device__ __forceinline__ void project_f16(cx<float> (&h0)[3], cx<float> (&h1)[3], const unsigned (&w)[12])
@@ -386,7 +386,7 @@ __device__ __forceinline__ void load_project(cx<typename Prec<P>::real> (&h0)[3]
     cx<T> q[12];
     if constexpr (P == WL_F16) {
         float nrm;
-#if WL_F16_MIXED_ADD
+#if WL_F16_MIXED_ADD && !WL_SPINOR16_FIXED
         (void)q;
         unsigned w[12];
         {

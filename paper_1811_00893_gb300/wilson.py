@@ -96,6 +96,7 @@ def load() -> ctypes.CDLL:
             "wilson_solve_batch": (I, [I, P, P, P, P, ctypes.POINTER(wl_solve_params),
                                        ctypes.POINTER(wl_solve_info), P]),
             "wl_last_error": (ctypes.c_char_p, []),
+            "wl_spinor16_format": (I, []),
             "wl_launch_count": (LL, []),
             "wl_algorithmic_bytes": (D, []),
             "wl_timing": (I, [P, I]),
@@ -114,6 +115,7 @@ def exported_symbols():
     return ["wl_gauge_create", "wl_gauge_destroy", "wl_half_volume", "wl_field_bytes",
             "wl_field_to_internal", "wl_field_to_canonical", "wilson_dslash", "wilson_mult",
             "wl_clover_set", "wl_clover_apply", "wl_cdot", "wl_cdot_noalloc", "wilson_solve", "wilson_solve_batch", "wl_last_error",
+            "wl_spinor16_format",
             "wl_launch_count", "wl_algorithmic_bytes", "wl_timing", "wl_timing_read"]
 
 
@@ -255,6 +257,11 @@ def wilson_solve_batch(gs, xs, bs, nrhs, params: wl_solve_params, stream=None, c
 
 def wl_last_error() -> str:
     return load().wl_last_error().decode()
+
+
+def wl_spinor16_format() -> int:
+    """0: binary16 spinor words (default build); 1: int16 fixed point."""
+    return int(load().wl_spinor16_format())
 
 
 def wl_launch_count() -> int:

@@ -76,6 +76,34 @@ def test_conversion_round_trip(case, prec):
             assert err < {"f32": 1e-7, "f16": 1.3e-3, "df64": 1e-14}[prec], err
 
 
+def test_f16_spinor_codec_error_bound(case):
+    """Each component of a stored WL_F16 spinor is within the rounding of the
+    build's 16-bit encoding (wl_spinor16_format) of the exact value.  With m the
+    site's max |component|, binary16 rounds v/m to 11 significant bits (2^-11
+    relative; 2^-25 absolute in the subnormal range), and int16 fixed point
+    rounds it to the nearest multiple of 1/32767.  The FP64 -> FP32 input
+    rounding, the FP32 scale 1/m and the product with m on the way back add a
+    few units of 2^-24 m.  The source spans eight decades within each site, so
+    it reaches binary16's subnormal range and the fixed-point format's
+    small-value end."""
+    psi = case.source(nrhs=1, seed=13)
+    g = torch.Generator().manual_seed(5)
+    psi = psi * torch.pow(10.0, -8.0 * torch.rand(psi.shape, generator=g, dtype=torch.float64)).cuda()
+    fmt = wilson.wl_spinor16_format()
+    assert fmt in (0, 1)
+    for p in (0, 1):
+        back = case.to_canonical(case.to_internal(psi, p, "f16"), p, "f16", nrhs=1)
+        w = case.half(psi, p).reshape(-1, 12).view(np.float64).reshape(-1, 24)
+        got = case.half(back, p).reshape(-1, 12).view(np.float64).reshape(-1, 24)
+        m = np.abs(w).max(axis=1, keepdims=True)
+        if fmt == 0:
+            bound = 2.0 ** -11 * np.abs(w) * (1 + 2.0 ** -20) + 2.0 ** -25 * m + 5 * 2.0 ** -24 * m
+        else:
+            bound = (0.5 / 32767 + 6 * 2.0 ** -24) * m
+        err = np.abs(got - w)
+        assert np.all(err <= bound), (fmt, p, float((err / bound).max()))
+
+
 # ----------------------------------------------------------------------------
 # a2: hopping term
 # ----------------------------------------------------------------------------
