@@ -20,7 +20,7 @@
 // inner precision, x += e in FP64.  With delta > 0 the inner Krylov space is
 // kept and only the residual is replaced (reliable updates, Sleijpen & van
 // der Vorst 1996); otherwise each inner solve restarts (defect correction).
-// Convergence is always judged on the FP64 true residual of the full D.
+// Convergence is always decided on the FP64 true residual of the full D.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
