@@ -1075,7 +1075,6 @@ int SolveState::finalize(bool* retry_out)
 int SolveState::end(wl_solve_info* info)
 {
     const size_t hb64 = w->hb64;
-    const long long V = 2 * g->geo.Vh;
     WL_TRY(field_to_canonical(g, xd, w->x64, 0, WL_F64, nrhs, s, 2 * (long long)hb64));
     WL_TRY(field_to_canonical(g, xd, (const char*)w->x64 + hb64, 1, WL_F64, nrhs, s, 2 * (long long)hb64));
     if (host_x) WL_CUDA(cudaMemcpyAsync(x_user, xd, canon, cudaMemcpyDeviceToHost, s));
