@@ -3,8 +3,9 @@
 // FP64 accumulation above the thread level, precision conversion, zeroing
 // and FP64 accumulation of a lower-precision correction.
 //
-// A vector is `nhalf` half fields per right-hand side stored back to back;
-// element j (one site) lives in half j / Vh at index j % Vh.  Each kernel
+// A vector is `nhalf` half fields per right-hand side stored back to back
+// (nhalf = 1 for even-odd vectors, 2 for full-lattice ones); element j (one
+// site) lives in half j / Vh at index j % Vh.  Each kernel
 // runs one thread per site and right-hand side (grid.y = rhs).
 #include <algorithm>
 #include <map>
@@ -67,7 +68,7 @@ struct Vec {
 __device__ __forceinline__ const char* at(const void* base, const Vec& v, int rhs, long long j,
                                           long long& i)
 {
-    const int h = (int)(j / v.Vh);
+    const int h = j >= v.Vh ? 1 : 0;  // nhalf <= 2: a comparison, not a 64-bit division
     i = j - h * v.Vh;
     return (const char*)base + rhs * v.rstride + h * v.hb;
 }
@@ -159,7 +160,7 @@ __global__ void accum_hi_kernel(void* xhi, Vec vh, const void* xlo, Vec vl, cons
     store_spinor<PH>(ph, vh.Vh, i, y);
 }
 
-static Vec make_vec(wl_gauge g, int prec, int nhalf, long long rs = 0)
+static Vec make_vec(wl_gauge g, int prec, int nhalf, long long rs = 0)  // nhalf is 1 or 2
 {
     Vec v;
     v.Vh = g->geo.Vh;

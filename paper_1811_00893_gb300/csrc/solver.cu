@@ -82,9 +82,11 @@ struct Vec2 {
     long long rstride;
 };
 
+// Half and site of element j.  A vector has one half (even-odd) or two (full
+// lattice), so the half is a comparison, not a 64-bit division.
 __device__ __forceinline__ long long split_index(const Vec2& v, long long j, long long& off)
 {
-    const int h = (int)(j / v.Vh);
+    const int h = j >= v.Vh ? 1 : 0;
     off = h * (long long)v.hb;
     return j - h * v.Vh;
 }
@@ -204,7 +206,7 @@ __global__ void init_scal_kernel(Scal* sc, const int* mask, int nrhs, int full)
 // host helpers
 // ---------------------------------------------------------------------------
 
-static Vec2 vec_of(wl_gauge g, int prec, int nhalf)
+static Vec2 vec_of(wl_gauge g, int prec, int nhalf)  // nhalf is 1 or 2
 {
     Vec2 v;
     v.Vh = g->geo.Vh;
