@@ -255,15 +255,19 @@ __global__ void __launch_bounds__(256) batch_update_xr_kernel(const BatchArgs B)
     __syncthreads();
     const double dc[4] = {dcoef[0], dcoef[1], dcoef[2], dcoef[3]};
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double part[3] = {0, 0, 0};
+    using T = typename Prec<P>::real;
+    T pt[3] = {0, 0, 0};
     if (i < L.g.Vh) {
         const long long o = ls.y * L.vb;
-        typename Prec<P>::real pt[3];
         xr_update_site<P, PX>(L.xlo + ls.y * L.xb, L.r + o, L.p + o, L.s + o, L.t + o, L.rh + o,
                               L.g.Vh, i, dc, pt);
-        for (int k = 0; k < 3; ++k) part[k] = (double)pt[k];
     }
-    block_sum<3>(part, sh);
+    // warp totals in the arithmetic type (FP32 for the narrow types), FP64 from there
+    typename RedType<T>::type wp[3] = {(typename RedType<T>::type)pt[0], (typename RedType<T>::type)pt[1],
+                                       (typename RedType<T>::type)pt[2]};
+    warp_sum<3>(wp);
+    double part[3] = {(double)wp[0], (double)wp[1], (double)wp[2]};
+    block_sum_warps<3>(part, sh);
     double tot[3];
     if (grid_sum<3>(part, tot, B.red, blockIdx.y, L.chunks, blockIdx.x, sh))
         advance_scalars(S, tot, dc);
