@@ -119,6 +119,7 @@ class ClockSampler:
         self.gpu_index = gpu_index
         self.proc = None
         self.lines = []
+        self.first = 0
 
     def start(self):
         try:
@@ -128,6 +129,13 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # nvidia-smi takes a moment to start: wait (bounded) for its first
+            # sample, so that the timed region that follows is sampled from its
+            # start; samples up to here are not the timed region's
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.first = len(self.lines)
         except (OSError, ValueError):
             self.proc = None
         return self
@@ -146,7 +154,10 @@ class ClockSampler:
             self.proc.kill()
         self.thread.join(timeout=2)
         sm, mx, reasons = [], [], set()
-        for ln in self.lines:
+        # the timed region's samples; a region shorter than the sampling period
+        # keeps the sample taken just before it
+        lines = self.lines[self.first:] or self.lines[-1:]
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
