@@ -207,7 +207,8 @@ typedef struct {
     int maxiter;       /* bound on inner iterations, per RHS */
     int eo;            /* 1: solve the even-odd Schur system M_ee x_e = b_e + kappa H_eo b_o */
     wl_prec inner;     /* precision of the Krylov iteration; WL_F64 = plain FP64 BiCGStab */
-    double inner_tol;  /* defect correction: relative tolerance of each inner solve (0: default) */
+    double inner_tol;  /* defect correction: relative tolerance of each inner solve (0: default,
+                          3e-6 for an FP32 inner solve, 1e-3 for FP16) */
     double delta;      /* > 0: reliable updates (recompute the FP64 residual when the iterated
                           residual drops below delta times its maximum since the last update)
                           instead of restarted defect correction */
