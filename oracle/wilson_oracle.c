@@ -509,7 +509,7 @@ int orc_solve(const double* U, const double* b, double* x, const int* L, const d
               double kappa, int eo, double tol, int maxiter, int* info, double* true_resid)
 {
     long V = volume(L), Vh = V / 2;
-    op_ctx c = {U, L, bc, kappa, eo};
+    op_ctx c = {U, L, bc, kappa, eo, NULL};
     int iters = 0, restarts = 0, status = 1, passes = 0;
     double bnorm = sqrt(norm2(V * NS * NC, b));
     double target = tol * bnorm;
@@ -564,7 +564,7 @@ int orc_bicgstab_fixed(const double* U, const double* b_sys, double* x_sys, cons
                        const double* bc, double kappa, int eo, int niter)
 {
     long n = (eo ? volume(L) / 2 : volume(L)) * NS * NC;
-    op_ctx c = {U, L, bc, kappa, eo};
+    op_ctx c = {U, L, bc, kappa, eo, NULL};
     int iters = 0, restarts = 0;
     return bicgstab(&c, n, b_sys, x_sys, 0.0, niter, &iters, &restarts);
 }
