@@ -9,7 +9,7 @@ time (Sec. 2 allows either condition per direction).
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 

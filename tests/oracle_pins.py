@@ -30,7 +30,6 @@ from __future__ import annotations
 import itertools
 
 import numpy as np
-import torch
 
 import oracle
 from paper_1811_00893_gb300 import fields

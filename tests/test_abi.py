@@ -5,8 +5,6 @@ import ctypes
 import os
 import re
 
-import pytest
-
 from paper_1811_00893_gb300 import wilson
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "wilson.h")
