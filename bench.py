@@ -242,7 +242,7 @@ SCHEMES = {  # workload scheme -> (inner precision name, solve parameters)
     "fp64": ("f64", dict(eo=False, inner=0)),
     "fp32-defect-correction": ("f32", dict(eo=True, inner=1)),
     "fp16-reliable": ("f16", dict(eo=True, inner=2, delta=0.003)),
-    "fp32-multirhs": ("f32", dict(eo=True, inner=1, graph_iters=8)),
+    "fp32-multirhs": ("f32", dict(eo=True, inner=1, graph_iters=4)),
 }
 
 
@@ -564,7 +564,7 @@ def run_batch(args, rank, world, local):
         xs.append(torch.zeros_like(bs[-1]))
     hs = [g.handle for g in gs]
     nr = [m.nrhs for m in spec]
-    p = wilson.solve_params(tol=1e-10, eo=True, inner=wilson.WL_F32, graph_iters=8)
+    p = wilson.solve_params(tol=1e-10, eo=True, inner=wilson.WL_F32, graph_iters=4)
     stream = torch.cuda.current_stream()
     for _ in range(max(3, args.warmup)):
         wilson.wilson_solve_batch(hs, xs, bs, nr, p)
@@ -635,8 +635,8 @@ def run_batch(args, rank, world, local):
         for g, x, b, n in zip(gs, xs, bs, nr):
             wilson.wilson_solve(g.handle, x, b, n, q)
 
-    seq_mixed_ms = timed(lambda: per_lattice(wilson.WL_F32, 8))
-    seq_fp64_ms = timed(lambda: per_lattice(wilson.WL_F64, 8))
+    seq_mixed_ms = timed(lambda: per_lattice(wilson.WL_F32, 4))
+    seq_fp64_ms = timed(lambda: per_lattice(wilson.WL_F64, 4))
     out = None
     if rank == 0:
         step_ms = ms / args.steps

@@ -25,7 +25,7 @@ pytestmark = pytest.mark.gpu
 # workload -> (storage precision of the hopping term, solve parameters), as in bench.SCHEMES
 SCHEMES = {"fp32-defect-correction": ("f32", dict(eo=True, inner=wilson.WL_F32)),
            "fp16-reliable": ("f16", dict(eo=True, inner=wilson.WL_F16, delta=0.003)),
-           "fp32-multirhs": ("f32", dict(eo=True, inner=wilson.WL_F32, graph_iters=8))}
+           "fp32-multirhs": ("f32", dict(eo=True, inner=wilson.WL_F32, graph_iters=4))}
 
 
 def sample_sites(dims, parity, n_random=256, seed=0):
