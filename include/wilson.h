@@ -76,7 +76,7 @@ enum {
     WL_ERR_NOT_CONVERGED = -3,  /* maxiter reached; x holds the best iterate */
     WL_ERR_BREAKDOWN = -4,      /* BiCGStab broke down more often than it may restart */
     WL_ERR_NAN = -5,            /* a reduction produced NaN or Inf */
-    WL_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up */
+    /* -6 is unused: no kernel of the library waits on another */
     WL_ERR_STATE = -7           /* the gauge object lacks what the call needs */
 };
 
@@ -189,16 +189,21 @@ int wl_cdot(wl_gauge g, double* out, const void* a, const void* b, wl_prec prec,
  * cudaMalloc behind it, latency-critical loops in which cudaMalloc/cudaFree
  * would synchronise the device, and callers holding raw field pointers but no
  * gauge object (wl_cdot keeps its scratch in the gauge object's workspace).
- * Same results as wl_cdot (up to summation order) for nrhs half fields of Vh
- * sites, stored back to back with stride wl_field_bytes(g, prec, 1); `out` is
- * device memory for 3*nrhs doubles.  Scratch is one fixed __device__ array of
- * WL_NOALLOC_MAX_RHS x WL_NOALLOC_BLOCKS x 3 doubles (768 KiB) that every GPU
- * loading the library holds until the process exits; nrhs above
- * WL_NOALLOC_MAX_RHS returns WL_ERR_ARG.  The first call on each device looks
- * up the array's device address (cudaGetSymbolAddress), so make that first
- * call before any stream capture.  All calls share the array and each call
- * overwrites what the previous one left: calls that overlap on the GPU race.
- * Never calls cudaMalloc, cudaFree or any allocating routine.  Asynchronous. */
+ * Same results as wl_cdot (up to summation order), in every precision
+ * including WL_DF64, for nrhs half fields of Vh sites, stored back to back
+ * with stride wl_field_bytes(g, prec, 1); `out` is device memory for 3*nrhs
+ * doubles.  WL_F16 needs Vh divisible by 4 (a field takes 52 Vh bytes and the
+ * next one must start on a 16-byte boundary; every lattice with even extents
+ * has Vh divisible by 8); WL_ERR_ARG otherwise.  Scratch is one fixed
+ * __device__ array of WL_NOALLOC_MAX_RHS x WL_NOALLOC_BLOCKS x 3 doubles
+ * (768 KiB) that every GPU loading the library holds until the process exits;
+ * nrhs above WL_NOALLOC_MAX_RHS returns WL_ERR_ARG.  Every call looks up the
+ * array's device address in the current context (cudaGetSymbolAddress, a
+ * host-side query), so it stays valid after the context is reset; the first
+ * call on a device may load the library's device code, so make it before any
+ * stream capture.  All calls share the array and each call overwrites what
+ * the previous one left: calls that overlap on the GPU race.  Never calls
+ * cudaMalloc, cudaFree or any allocating routine.  Asynchronous. */
 int wl_cdot_noalloc(double* out, const void* a, const void* b, long long Vh, wl_prec prec,
                     int nrhs, void* stream);
 
@@ -250,6 +255,81 @@ int wilson_solve(wl_gauge g, double* x, const double* b, int nrhs, const wl_solv
 int wilson_solve_batch(int nlat, const wl_gauge* gs, double* const* x, const double* const* b,
                        const int* nrhs, const wl_solve_params* p, wl_solve_info* info,
                        void* stream);
+
+/* ------------------------------------------------------------------------
+ * Domain decomposition (Sec. 4.4 "Thread Task Assignment"; the multi-node
+ * setting of Sec. 5.2.3 and Sec. 6).
+ *
+ * The lattice is cut into grid[1] x grid[2] x grid[3] equal blocks along y, z
+ * and t (grid[0] must be 1: x is never cut, as in Sec. 4.1); block extents
+ * must be even and >= 2.  Block k has coordinates (0, k % g1, (k / g1) % g2,
+ * k / (g1 g2)) and holds the sites whose global coordinates lie in
+ * [coord_mu * L_mu / grid_mu, (coord_mu + 1) * L_mu / grid_mu).  Each block is
+ * a gauge object (wl_dd_block) with its own link copies; its fields are the
+ * library's internal half fields of the block lattice (wl_field_bytes,
+ * wl_field_to_internal / wl_field_to_canonical on the block's gauge object,
+ * with block-local canonical fields).  The hopping term of a block reads the
+ * neighbouring blocks' spinors through halo buffers: each application packs
+ * the spin-projected half spinors of the cut faces (12 reals per face site),
+ * moves them to the neighbours' halos (device copies on a second stream, or,
+ * in the direct mode, written there by the pack kernel itself), computes the
+ * interior sites while the faces move, then the boundary sites.  Global sums
+ * are formed per block and added over the blocks in block order.  Results
+ * equal those of the undivided lattice up to the summation order of the
+ * global sums.
+ *
+ * All blocks live on the calling thread's current GPU.  The calls are
+ * asynchronous on `stream` except wl_dd_create, wl_dd_destroy,
+ * wl_dd_set_exchange and wilson_solve_dd.  Block gauge objects belong to the
+ * decomposition: wilson_dslash, wilson_mult, wilson_solve(_batch) and
+ * wl_clover_set refuse them (WL_ERR_STATE); there is no clover term in the
+ * decomposed operator.
+ * ---------------------------------------------------------------------- */
+typedef struct wl_dd_s* wl_dd;
+
+/* Create a decomposition of the lattice `lat` into grid[0..3] blocks (at most
+ * 16), its links from the canonical FP64 gauge field U of the whole lattice
+ * (device memory, read during the call).  prec_mask as for wl_gauge_create. */
+int wl_dd_create(wl_dd* dd, const wl_lattice* lat, const int grid[4], const double* U, int prec_mask,
+                 void* stream);
+int wl_dd_destroy(wl_dd dd);
+/* Number of blocks (0 for NULL). */
+int wl_dd_blocks(wl_dd dd);
+/* Gauge object and grid coordinates of block k (either output may be NULL). */
+int wl_dd_block(wl_dd dd, int k, wl_gauge* g, int coord[4]);
+/* Exchange of the packed faces: 0 = the pack kernel writes the block's own
+ * send buffer and cudaMemcpyAsync moves each face to the neighbour's halo on
+ * a second stream, overlapping the interior sweep (the default); 1 = the pack
+ * kernel writes straight into the neighbours' halos.  Synchronises the
+ * device. */
+int wl_dd_set_exchange(wl_dd dd, int mode);
+
+/* Copy nrhs canonical FP64 fields of the whole lattice (`global`, device,
+ * nrhs*V*12 complex) to block-local canonical fields (local[k], device,
+ * nrhs*V_block*12 complex), and back.  Asynchronous. */
+int wl_dd_scatter(wl_dd dd, double* const* local, const double* global, int nrhs, void* stream);
+int wl_dd_gather(wl_dd dd, double* global, const double* const* local, int nrhs, void* stream);
+
+/* wilson_dslash on the decomposed lattice: out[k] = H_{p,1-p} in[k] for every
+ * block k (internal half fields of the block lattice, nrhs back to back). */
+int wilson_dslash_dd(wl_dd dd, void* const* out, const void* const* in, int out_parity, int dagger,
+                     wl_prec prec, int nrhs, void* stream);
+/* wilson_mult on the decomposed lattice (eo = 0: full D on [even | odd]
+ * block fields; eo = 1: M_ee on even block fields). */
+int wilson_mult_dd(wl_dd dd, void* const* out, const void* const* in, int eo, int dagger, wl_prec prec,
+                   int nrhs, void* stream);
+/* wl_cdot over the whole lattice: each block's local sums, then their total
+ * (the allreduce) in out (device, 3*nrhs doubles). */
+int wl_cdot_dd(wl_dd dd, double* out, const void* const* a, const void* const* b, wl_prec prec, int nrhs,
+               void* stream);
+/* wilson_solve on the decomposed lattice: every inner iteration applies the
+ * decomposed M_ee (two halo exchanges) and sums its dot products over the
+ * blocks (one allreduce per reduction).  x[k], b[k]: block-local canonical
+ * FP64 fields (device), nrhs each.  Even-odd systems only (p->eo = 1), eager
+ * launches (graph_iters is read as the host-check interval).  info has nrhs
+ * entries.  Synchronises the stream. */
+int wilson_solve_dd(wl_dd dd, double* const* x, const double* const* b, int nrhs, const wl_solve_params* p,
+                    wl_solve_info* info, void* stream);
 
 /* Encoding of the 16-bit words of WL_F16 spinors in this build.  Both forms
  * store each value divided by its site's max |component| (the FP32 norm kept

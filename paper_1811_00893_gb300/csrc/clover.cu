@@ -257,6 +257,7 @@ extern "C" int wl_clover_set(wl_gauge g, const double* F, void* stream)
 {
     WL_ENTRY();
     if (!g) return set_error(WL_ERR_ARG, "NULL gauge object");
+    if (g->dd_part) return set_error(WL_ERR_STATE, "block of a domain decomposition: use the _dd calls");
     cudaStream_t s = (cudaStream_t)stream;
     if (!F) {
         WL_CUDA(cudaStreamSynchronize(s));

@@ -1,0 +1,598 @@
+// Host side of the domain decomposition (dd.cuh): the block objects, halo
+// regions, the exchange of packed faces, the launch sequence of one
+// decomposed hopping application (Sec. 4.4: pack -> exchange || interior ->
+// boundary) and the sum of the blocks' local reductions.  Entry points:
+// wl_dd_create / destroy / blocks / block / set_exchange, wl_dd_scatter /
+// gather, wilson_dslash_dd, wilson_mult_dd, wl_cdot_dd.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "dd_kernels.cuh"
+
+namespace wl {
+
+extern template struct DDKernels<0>;  // dd_hop.cu
+extern template struct DDKernels<1>;  // dd_hop_r12.cu
+
+// ---------------------------------------------------------------------------
+// canonical global field <-> block-local canonical fields
+// ---------------------------------------------------------------------------
+
+struct Origin {
+    int o[4];
+};
+
+// dir = 0: local <- global; dir = 1: global <- local
+__global__ void dd_copy_canonical_kernel(double* loc, double* glob, Geom gl, Geom gg, Origin org,
+                                         long long Vl, long long Vg, int dir)
+{
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int rhs = blockIdx.y;
+    if (s >= Vl) return;
+    long long r = s;
+    int c[4];
+    for (int mu = 0; mu < 4; ++mu) {
+        c[mu] = (int)(r % gl.L[mu]) + org.o[mu];
+        r /= gl.L[mu];
+    }
+    const long long sg = c[0] + (long long)gg.L[0] * (c[1] + (long long)gg.L[1] * (c[2] + (long long)gg.L[2] * c[3]));
+    double2* pl = (double2*)(loc + ((long long)rhs * Vl + s) * 24);
+    double2* pg = (double2*)(glob + ((long long)rhs * Vg + sg) * 24);
+    if (dir == 0)
+        for (int k = 0; k < 12; ++k) pl[k] = pg[k];
+    else
+        for (int k = 0; k < 12; ++k) pg[k] = pl[k];
+}
+
+// ---------------------------------------------------------------------------
+// sums over the blocks
+// ---------------------------------------------------------------------------
+
+struct DDFinish {
+    const double* partial;  // block partials (fused hop reductions), or
+    const double* loc[kMaxDomains];  // per-block local 3-tuples (nblocks = 0)
+    long long dom_stride;
+    int max_blocks, nblocks, ndom;
+    double* out[kMaxDomains];
+    int out_stride;
+    const int* active;  // right-hand-side flags (every block holds the same)
+    int active_stride;
+};
+
+// One block per right-hand side: the total over the blocks, in block order
+// (the allreduce), written for every block.
+__global__ void __launch_bounds__(256) dd_finish_kernel(const DDFinish F)
+{
+    const int rhs = blockIdx.x;
+    if (F.active && !F.active[(long long)rhs * F.active_stride]) return;
+    __shared__ double sh[3 * 32];
+    double tot[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < F.ndom; ++d) {
+        double v[3];
+        if (F.nblocks > 0) {
+            sum_partials<3>(F.partial + d * F.dom_stride + (long long)rhs * F.max_blocks * 3, F.nblocks, v);
+            block_sum<3>(v, sh);
+        } else {
+            for (int k = 0; k < 3; ++k) v[k] = F.loc[d][3 * rhs + k];
+        }
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 3; ++k) tot[k] += v[k];
+    }
+    if (threadIdx.x == 0)
+        for (int d = 0; d < F.ndom; ++d)
+            if (F.out[d])
+                for (int k = 0; k < 3; ++k) F.out[d][(long long)rhs * F.out_stride + k] = tot[k];
+}
+
+int dd_allreduce(wl_dd dd, double* const* loc, double* const* out, int out_stride, int nrhs,
+                 const int* const* active, int active_stride, cudaStream_t s)
+{
+    DDFinish F;
+    std::memset(&F, 0, sizeof F);
+    F.nblocks = 0;
+    F.ndom = dd->ndom;
+    for (int d = 0; d < dd->ndom; ++d) {
+        F.loc[d] = loc[d];
+        F.out[d] = out[d];
+    }
+    F.out_stride = out_stride;
+    F.active = active ? active[0] : nullptr;
+    F.active_stride = active_stride;
+    dd_finish_kernel<<<nrhs, 256, 0, s>>>(F);
+    WL_CHECK_LAUNCH(0.0);
+    return WL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// buffers
+// ---------------------------------------------------------------------------
+
+static int ensure_regions(wl_dd dd, size_t bytes)
+{
+    if (bytes <= dd->region_bytes) return WL_OK;
+    WL_CUDA(cudaDeviceSynchronize());
+    for (int d = 0; d < dd->ndom; ++d) {
+        if (dd->recv[d]) cudaFree(dd->recv[d]);
+        if (dd->send[d]) cudaFree(dd->send[d]);
+        dd->recv[d] = dd->send[d] = nullptr;
+    }
+    dd->region_bytes = 0;
+    for (int d = 0; d < dd->ndom; ++d) {
+        WL_CUDA(cudaMalloc((void**)&dd->recv[d], bytes));
+        WL_CUDA(cudaMalloc((void**)&dd->send[d], bytes));
+    }
+    dd->region_bytes = bytes;
+    return WL_OK;
+}
+
+static int ensure_partials(wl_dd dd, int nrhs, int blocks)
+{
+    if (nrhs <= dd->part_rhs && blocks <= dd->part_max_blocks) return WL_OK;
+    WL_CUDA(cudaDeviceSynchronize());
+    if (dd->partial) cudaFree(dd->partial);
+    dd->partial = nullptr;
+    dd->part_rhs = std::max(nrhs, dd->part_rhs);
+    dd->part_max_blocks = std::max(blocks, dd->part_max_blocks);
+    dd->part_dom_stride = (long long)dd->part_rhs * dd->part_max_blocks * 3;
+    WL_CUDA(cudaMalloc((void**)&dd->partial, sizeof(double) * dd->part_dom_stride * dd->ndom));
+    return WL_OK;
+}
+
+static int ensure_loc(wl_dd dd, int nrhs)
+{
+    if (nrhs <= dd->loc_rhs) return WL_OK;
+    WL_CUDA(cudaDeviceSynchronize());
+    if (dd->loc) cudaFree(dd->loc);
+    dd->loc = nullptr;
+    WL_CUDA(cudaMalloc((void**)&dd->loc, sizeof(double) * 3 * nrhs * dd->ndom));
+    dd->loc_rhs = nrhs;
+    return WL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one decomposed hopping application
+// ---------------------------------------------------------------------------
+
+int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
+{
+    const int P = h.prec;
+    for (int d = 0; d < dd->ndom; ++d)
+        if (!dd->dom[d]->links[P][0])
+            return set_error(WL_ERR_STATE, "domain decomposition was created without the requested precision");
+    static const bool r12_off = getenv("WL_NO_R12") != nullptr;
+    const int lf = (P == WL_F32 || P == WL_F16) && dd->dom[0]->links_r12[P][0] && !r12_off ? 1 : 0;
+    const int np = h.nparity, nrhs = h.nrhs;
+    const Geom& g = dd->gloc;
+    const long long hsb = (long long)halo_site_bytes(P);
+
+    // halo segments of (launch parity, mu, side), all right-hand sides each
+    long long hoff[2][4][2] = {};
+    long long off = 0;
+    DDSeg seg[12];
+    int nseg = 0;
+    long long total = 0;
+    for (int k = 0; k < np; ++k)
+        for (int mu = 1; mu < 4; ++mu)
+            if (dd->cut & (1 << mu))
+                for (int side = 0; side < 2; ++side) {
+                    hoff[k][mu][side] = off;
+                    off += dd->fs[mu] * hsb * nrhs;
+                    seg[nseg++] = {k, mu, side, total, dd->fs[mu]};
+                    total += dd->fs[mu];
+                }
+    WL_TRY(ensure_regions(dd, (size_t)off));
+    const size_t sb = spinor_field_bytes(P, 1);
+
+    // 1. pack, 2. exchange
+    if (nseg) {
+        DDPackArgs PA;
+        std::memset(&PA, 0, sizeof PA);
+        PA.g = g;
+        std::memcpy(PA.seg, seg, sizeof seg);
+        PA.nseg = nseg;
+        PA.total = total;
+        std::memcpy(PA.hoff, hoff, sizeof hoff);
+        PA.rs_in = h.rs_in;
+        for (int d = 0; d < dd->ndom; ++d) {
+            for (int k = 0; k < np; ++k) PA.in[d][k] = (const char*)h.in[d][k];
+            for (int mu = 1; mu < 4; ++mu)
+                for (int side = 0; side < 2; ++side) {
+                    // side 0 feeds the backward neighbour, side 1 the forward one
+                    const int to = dd->peer[d][mu][side];
+                    PA.dst[d][mu][side] = dd->direct ? dd->recv[to] : dd->send[d];
+                }
+        }
+        const dim3 grid((unsigned)((total + kDDBlock - 1) / kDDBlock), (unsigned)nrhs, (unsigned)dd->ndom);
+        DDKernels<0>::pack(P, h.dagger != 0, PA, grid, s);
+        WL_CHECK_LAUNCH((double)nrhs * dd->ndom * total * (sb + hsb));
+        if (!dd->direct) {
+            WL_CUDA(cudaEventRecord(dd->ev_packed, s));
+            WL_CUDA(cudaStreamWaitEvent(dd->comm, dd->ev_packed, 0));
+            for (int d = 0; d < dd->ndom; ++d)
+                for (int k = 0; k < nseg; ++k) {
+                    const DDSeg& S = seg[k];
+                    const int to = dd->peer[d][S.mu][S.side];
+                    const long long o = hoff[S.pidx][S.mu][S.side];
+                    WL_CUDA(cudaMemcpyAsync(dd->recv[to] + o, dd->send[d] + o, (size_t)(S.count * hsb * nrhs),
+                                            cudaMemcpyDeviceToDevice, dd->comm));
+                }
+            WL_CUDA(cudaEventRecord(dd->ev_exchanged, dd->comm));
+        }
+    }
+
+    // 3. interior, 4. boundary
+    DDArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.g = g;
+    for (int mu = 1; mu < 4; ++mu)
+        if (dd->cut & (1 << mu)) {
+            A.cutmask |= 3u << (2 * mu);
+            A.fs[mu] = dd->fs[mu];
+        }
+    std::memcpy(A.hoff, hoff, sizeof hoff);
+    A.active_stride = h.active_stride;
+    A.parity0 = h.parity0;
+    A.rs_in = h.rs_in;
+    A.rs_out = h.rs_out;
+    A.rs_x1 = h.rs_x1;
+    A.rs_x2 = h.rs_x2;
+    A.rs_w = h.rs_w;
+    A.a = h.a;
+    A.b1 = h.b1;
+    for (int mu = 0; mu < 4; ++mu) A.ph[mu] = {(float)dd->global.bc_re[mu], (float)dd->global.bc_im[mu]};
+    for (int d = 0; d < dd->ndom; ++d) {
+        DDDom& D = A.d[d];
+        wl_gauge gd = dd->dom[d];
+        for (int k = 0; k < np; ++k) {
+            const int p = h.parity0 + k;
+            D.links[k] = lf ? gd->links_r12[P][p] : gd->links[P][p];
+            D.in[k] = (const char*)h.in[d][k];
+            D.out[k] = (char*)h.out[d][k];
+            D.x1[k] = (const char*)h.x1[d][k];
+            D.x2[k] = (const char*)h.x2[d][k];
+            D.w[k] = (const char*)h.w[d][k];
+        }
+        D.halo = dd->recv[d];
+        D.active = h.active[d];
+        D.edge = dd->edge[d];
+    }
+    const int bi = (int)((dd->nint + kDDBlock - 1) / kDDBlock);
+    const int bb = (int)((dd->nbnd + kDDBlock - 1) / kDDBlock);
+    if (h.dot) {
+        WL_TRY(ensure_partials(dd, nrhs, np * (bi + bb)));
+        A.partial = dd->partial;
+        A.dom_stride = dd->part_dom_stride;
+        A.max_blocks = dd->part_max_blocks;
+    }
+    const int extra = (h.x1[0][0] ? 1 : 0) + (h.x2[0][0] ? 1 : 0) + (h.w[0][0] ? 1 : 0);
+    const double site_bytes = (double)(lf ? (P == WL_F32 ? 384 : 192) : link_field_bytes(P, 1)) +
+                              (double)nrhs * (2 + extra) * sb;
+    auto run = [&](bool bnd) -> int {
+        const long long n = bnd ? dd->nbnd : dd->nint;
+        if (n == 0) return WL_OK;
+        A.sites = bnd ? dd->bsites : dd->isites;
+        A.nsites = n;
+        A.blocks_per_parity = bnd ? bb : bi;
+        A.block0 = bnd ? np * bi : 0;
+        const dim3 grid((unsigned)(A.blocks_per_parity * np), (unsigned)nrhs, (unsigned)dd->ndom);
+        if (lf) DDKernels<1>::hop(P, h.dagger != 0, h.dot, bnd, A, grid, s);
+        else DDKernels<0>::hop(P, h.dagger != 0, h.dot, bnd, A, grid, s);
+        WL_CHECK_LAUNCH((double)dd->ndom * np * n * site_bytes);
+        return WL_OK;
+    };
+    WL_TRY(run(false));
+    if (nseg && !dd->direct) WL_CUDA(cudaStreamWaitEvent(s, dd->ev_exchanged, 0));
+    WL_TRY(run(true));
+
+    // 5. the fused reductions, summed over the blocks
+    if (h.dot) {
+        DDFinish F;
+        std::memset(&F, 0, sizeof F);
+        F.partial = dd->partial;
+        F.dom_stride = dd->part_dom_stride;
+        F.max_blocks = dd->part_max_blocks;
+        F.nblocks = np * (bi + bb);
+        F.ndom = dd->ndom;
+        for (int d = 0; d < dd->ndom; ++d) F.out[d] = h.dot_out[d];
+        F.out_stride = h.dot_stride;
+        F.active = h.active[0];
+        F.active_stride = h.active_stride;
+        dd_finish_kernel<<<nrhs, 256, 0, s>>>(F);
+        WL_CHECK_LAUNCH(0.0);
+    }
+    return WL_OK;
+}
+
+}  // namespace wl
+
+using namespace wl;
+
+// ---------------------------------------------------------------------------
+// C entry points
+// ---------------------------------------------------------------------------
+
+extern "C" int wl_dd_destroy(wl_dd dd)
+{
+    if (!dd) return WL_OK;
+    cudaDeviceSynchronize();
+    dd_free_solver(dd);
+    for (int d = 0; d < dd->ndom; ++d) {
+        if (dd->dom[d]) wl_gauge_destroy(dd->dom[d]);
+        if (dd->recv[d]) cudaFree(dd->recv[d]);
+        if (dd->send[d]) cudaFree(dd->send[d]);
+    }
+    if (dd->isites) cudaFree(dd->isites);
+    if (dd->bsites) cudaFree(dd->bsites);
+    if (dd->partial) cudaFree(dd->partial);
+    if (dd->loc) cudaFree(dd->loc);
+    if (dd->ev_packed) cudaEventDestroy(dd->ev_packed);
+    if (dd->ev_exchanged) cudaEventDestroy(dd->ev_exchanged);
+    if (dd->comm) cudaStreamDestroy(dd->comm);
+    delete dd;
+    return WL_OK;
+}
+
+extern "C" int wl_dd_create(wl_dd* out, const wl_lattice* lat, const int* grid, const double* U, int prec_mask,
+                            void* stream)
+{
+    WL_ENTRY();
+    if (!out) return set_error(WL_ERR_ARG, "NULL output handle");
+    *out = nullptr;
+    WL_TRY(validate_lattice(lat));
+    if (!grid) return set_error(WL_ERR_ARG, "NULL block grid");
+    if (grid[0] != 1) return set_error(WL_ERR_ARG, "the x direction is never cut: grid[0] must be 1");
+    int ndom = 1;
+    wl_lattice loc = *lat;
+    for (int mu = 1; mu < 4; ++mu) {
+        if (grid[mu] < 1) return set_error(WL_ERR_ARG, "grid entries must be >= 1");
+        if (lat->dims[mu] % grid[mu]) return set_error(WL_ERR_ARG, "grid must divide the lattice extents");
+        loc.dims[mu] = lat->dims[mu] / grid[mu];
+        if (loc.dims[mu] < 2 || loc.dims[mu] % 2)
+            return set_error(WL_ERR_ARG, "block extents must be even and >= 2");
+        ndom *= grid[mu];
+    }
+    if (ndom > kMaxDomains) return set_error(WL_ERR_ARG, "at most 16 blocks per decomposition");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto dd = new wl_dd_s();
+    dd->global = *lat;
+    dd->gglob = make_geom(lat->dims);
+    dd->gloc = make_geom(loc.dims);
+    for (int mu = 0; mu < 4; ++mu) dd->grid[mu] = grid[mu];
+    dd->ndom = ndom;
+    for (int mu = 1; mu < 4; ++mu)
+        if (grid[mu] > 1) {
+            dd->cut |= 1 << mu;
+            dd->fs[mu] = dd->gloc.Vh / loc.dims[mu];
+        }
+    int rc = WL_OK;
+    do {
+        if (cudaGetDevice(&dd->device) != cudaSuccess) { rc = set_error(WL_ERR_CUDA, "cudaGetDevice"); break; }
+        for (int d = 0; d < ndom && rc == WL_OK; ++d) {
+            int c[4] = {0, d % grid[1], (d / grid[1]) % grid[2], d / (grid[1] * grid[2])};
+            int org[4];
+            for (int mu = 0; mu < 4; ++mu) {
+                dd->coord[d][mu] = c[mu];
+                org[mu] = c[mu] * loc.dims[mu];
+            }
+            for (int mu = 0; mu < 4; ++mu)
+                for (int side = 0; side < 2; ++side) {
+                    int cc[4] = {c[0], c[1], c[2], c[3]};
+                    cc[mu] = (c[mu] + (side ? 1 : grid[mu] - 1)) % grid[mu];
+                    dd->peer[d][mu][side] = cc[1] + grid[1] * (cc[2] + grid[2] * cc[3]);
+                }
+            unsigned edge = 0;
+            for (int mu = 0; mu < 4; ++mu) {
+                if (c[mu] == grid[mu] - 1) edge |= 1u << (2 * mu);  // forward face is the lattice's
+                if (c[mu] == 0) edge |= 1u << (2 * mu + 1);
+            }
+            dd->edge[d] = edge;
+            rc = gauge_create(&dd->dom[d], &loc, lat, org, U, prec_mask, s);
+            if (rc == WL_OK) dd->dom[d]->dd_part = 1;
+        }
+        if (rc != WL_OK) break;
+        // interior / boundary half indices of a block
+        const Geom& g = dd->gloc;
+        std::vector<int> is, bs;
+        for (long long i = 0; i < g.Vh; ++i) {
+            const long long row = i / g.Lxh;
+            const int c[4] = {0, (int)(row % g.L[1]), (int)((row / g.L[1]) % g.L[2]), (int)(row / ((long long)g.L[1] * g.L[2]))};
+            bool b = false;
+            for (int mu = 1; mu < 4; ++mu)
+                if ((dd->cut >> mu) & 1) b |= c[mu] == 0 || c[mu] == g.L[mu] - 1;
+            (b ? bs : is).push_back((int)i);
+        }
+        dd->nint = (long long)is.size();
+        dd->nbnd = (long long)bs.size();
+        if (cudaMalloc((void**)&dd->isites, sizeof(int) * std::max<size_t>(1, is.size())) != cudaSuccess ||
+            cudaMalloc((void**)&dd->bsites, sizeof(int) * std::max<size_t>(1, bs.size())) != cudaSuccess) {
+            cudaGetLastError();
+            rc = set_error(WL_ERR_CUDA, "cudaMalloc site lists");
+            break;
+        }
+        if ((!is.empty() && cudaMemcpy(dd->isites, is.data(), sizeof(int) * is.size(), cudaMemcpyHostToDevice) != cudaSuccess) ||
+            (!bs.empty() && cudaMemcpy(dd->bsites, bs.data(), sizeof(int) * bs.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
+            rc = set_error(WL_ERR_CUDA, "site list upload");
+            break;
+        }
+        if (cudaStreamCreateWithFlags(&dd->comm, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&dd->ev_packed, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&dd->ev_exchanged, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            rc = set_error(WL_ERR_CUDA, "exchange stream / events");
+            break;
+        }
+        const char* e = getenv("WL_DD_EXCHANGE");
+        dd->direct = (e && std::strcmp(e, "direct") == 0) ? 1 : 0;
+    } while (0);
+    if (rc != WL_OK) {
+        wl_dd_destroy(dd);
+        return rc;
+    }
+    *out = dd;
+    return WL_OK;
+}
+
+extern "C" int wl_dd_blocks(wl_dd dd) { return dd ? dd->ndom : 0; }
+
+extern "C" int wl_dd_block(wl_dd dd, int k, wl_gauge* g, int* coord)
+{
+    if (!dd) return set_error(WL_ERR_ARG, "NULL decomposition");
+    if (k < 0 || k >= dd->ndom) return set_error(WL_ERR_ARG, "block index out of range");
+    if (g) *g = dd->dom[k];
+    if (coord)
+        for (int mu = 0; mu < 4; ++mu) coord[mu] = dd->coord[k][mu];
+    return WL_OK;
+}
+
+extern "C" int wl_dd_set_exchange(wl_dd dd, int mode)
+{
+    if (!dd) return set_error(WL_ERR_ARG, "NULL decomposition");
+    if (mode != 0 && mode != 1) return set_error(WL_ERR_ARG, "exchange mode must be 0 (copy) or 1 (direct)");
+    cudaDeviceSynchronize();
+    dd->direct = mode;
+    return WL_OK;
+}
+
+static int dd_canonical(wl_dd dd, double* const* loc, double* glob, int nrhs, int dir, cudaStream_t s)
+{
+    if (!dd) return set_error(WL_ERR_ARG, "NULL decomposition");
+    if (!loc || !glob) return set_error(WL_ERR_ARG, "NULL pointer");
+    if (nrhs < 1 || nrhs > 65535) return set_error(WL_ERR_ARG, "nrhs must be in 1..65535");
+    const long long Vl = 2 * dd->gloc.Vh, Vg = 2 * dd->gglob.Vh;
+    for (int d = 0; d < dd->ndom; ++d) {
+        if (!loc[d]) return set_error(WL_ERR_ARG, "NULL block field");
+        Origin org;
+        for (int mu = 0; mu < 4; ++mu) org.o[mu] = dd->coord[d][mu] * dd->gloc.L[mu];
+        const dim3 grid((unsigned)((Vl + 127) / 128), (unsigned)nrhs);
+        dd_copy_canonical_kernel<<<grid, 128, 0, s>>>(loc[d], glob, dd->gloc, dd->gglob, org, Vl, Vg, dir);
+        WL_CHECK_LAUNCH(2.0 * 192.0 * Vl * nrhs);
+    }
+    return WL_OK;
+}
+
+extern "C" int wl_dd_scatter(wl_dd dd, double* const* local, const double* global, int nrhs, void* stream)
+{
+    WL_ENTRY();
+    return dd_canonical(dd, local, (double*)global, nrhs, 0, (cudaStream_t)stream);
+}
+
+extern "C" int wl_dd_gather(wl_dd dd, double* global, const double* const* local, int nrhs, void* stream)
+{
+    WL_ENTRY();
+    return dd_canonical(dd, (double* const*)local, global, nrhs, 1, (cudaStream_t)stream);
+}
+
+static int dd_check(wl_dd dd, const void* const* out, const void* const* in, wl_prec prec, int nrhs, int nhalf)
+{
+    if (!dd) return set_error(WL_ERR_ARG, "NULL decomposition");
+    if (prec < WL_F64 || prec > WL_DF64) return set_error(WL_ERR_ARG, "unknown precision");
+    if (nrhs < 1 || nrhs > 65535) return set_error(WL_ERR_ARG, "nrhs must be in 1..65535");
+    if (!out || !in) return set_error(WL_ERR_ARG, "NULL pointer");
+    const size_t fb = spinor_field_bytes(prec, dd->gloc.Vh) * nhalf * nrhs;
+    for (int d = 0; d < dd->ndom; ++d) {
+        if (!out[d] || !in[d]) return set_error(WL_ERR_ARG, "NULL block field");
+        if (!dd->dom[d]->links[prec][0])
+            return set_error(WL_ERR_STATE, "decomposition was created without this precision");
+        if (dd->dom[d]->has_clover)
+            return set_error(WL_ERR_STATE, "the decomposed operator has no clover term");
+        const char *o = (const char*)out[d], *i = (const char*)in[d];
+        if (o < i + fb && i < o + fb) return set_error(WL_ERR_ARG, "out and in overlap");
+    }
+    return WL_OK;
+}
+
+extern "C" int wilson_dslash_dd(wl_dd dd, void* const* out, const void* const* in, int out_parity, int dagger,
+                                wl_prec prec, int nrhs, void* stream)
+{
+    WL_ENTRY();
+    WL_TRY(dd_check(dd, (const void* const*)out, in, prec, nrhs, 1));
+    if (out_parity != 0 && out_parity != 1) return set_error(WL_ERR_ARG, "out_parity must be 0 or 1");
+    const size_t fb = spinor_field_bytes(prec, dd->gloc.Vh);
+    DDLaunch h;
+    h.prec = prec;
+    h.dagger = dagger ? 1 : 0;
+    h.parity0 = out_parity;
+    h.nrhs = nrhs;
+    for (int d = 0; d < dd->ndom; ++d) {
+        h.in[d][0] = in[d];
+        h.out[d][0] = out[d];
+    }
+    h.rs_in = h.rs_out = (long long)fb;
+    return dd_launch_hop(dd, h, (cudaStream_t)stream);
+}
+
+extern "C" int wilson_mult_dd(wl_dd dd, void* const* out, const void* const* in, int eo, int dagger, wl_prec prec,
+                              int nrhs, void* stream)
+{
+    WL_ENTRY();
+    WL_TRY(dd_check(dd, (const void* const*)out, in, prec, nrhs, eo ? 1 : 2));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t fb = spinor_field_bytes(prec, dd->gloc.Vh);
+    const double kappa = dd->global.kappa;
+    if (!eo) {  // out_p = in_p - kappa H in_{1-p} on [even | odd] block fields
+        DDLaunch h;
+        h.prec = prec;
+        h.dagger = dagger ? 1 : 0;
+        h.parity0 = 0;
+        h.nparity = 2;
+        h.nrhs = nrhs;
+        for (int d = 0; d < dd->ndom; ++d) {
+            h.in[d][0] = (const char*)in[d] + fb;
+            h.in[d][1] = in[d];
+            h.out[d][0] = out[d];
+            h.out[d][1] = (char*)out[d] + fb;
+            h.x1[d][0] = in[d];
+            h.x1[d][1] = (const char*)in[d] + fb;
+        }
+        h.rs_in = h.rs_out = h.rs_x1 = (long long)(2 * fb);
+        h.a = -kappa;
+        return dd_launch_hop(dd, h, s);
+    }
+    // M_ee = 1 - kappa^2 H_eo H_oe, through each block's odd temporary
+    for (int d = 0; d < dd->ndom; ++d) WL_TRY(ensure_tmp(dd->dom[d], prec, fb * nrhs));
+    DDLaunch h1;
+    h1.prec = prec;
+    h1.dagger = dagger ? 1 : 0;
+    h1.parity0 = 1;
+    h1.nrhs = nrhs;
+    for (int d = 0; d < dd->ndom; ++d) {
+        h1.in[d][0] = in[d];
+        h1.out[d][0] = dd->dom[d]->tmp[prec];
+    }
+    h1.rs_in = h1.rs_out = (long long)fb;
+    WL_TRY(dd_launch_hop(dd, h1, s));
+    DDLaunch h2 = h1;
+    h2.parity0 = 0;
+    for (int d = 0; d < dd->ndom; ++d) {
+        h2.in[d][0] = dd->dom[d]->tmp[prec];
+        h2.out[d][0] = out[d];
+        h2.x1[d][0] = in[d];
+    }
+    h2.rs_x1 = (long long)fb;
+    h2.a = -kappa * kappa;
+    return dd_launch_hop(dd, h2, s);
+}
+
+extern "C" int wl_cdot_dd(wl_dd dd, double* out, const void* const* a, const void* const* b, wl_prec prec, int nrhs,
+                          void* stream)
+{
+    WL_ENTRY();
+    if (!dd) return set_error(WL_ERR_ARG, "NULL decomposition");
+    if (!out || !a || !b) return set_error(WL_ERR_ARG, "NULL pointer");
+    if (prec < WL_F64 || prec > WL_DF64) return set_error(WL_ERR_ARG, "unknown precision");
+    if (nrhs < 1 || nrhs > 65535) return set_error(WL_ERR_ARG, "nrhs must be in 1..65535");
+    cudaStream_t s = (cudaStream_t)stream;
+    WL_TRY(ensure_loc(dd, nrhs));
+    double* loc[kMaxDomains];
+    double* outs[kMaxDomains] = {};
+    for (int d = 0; d < dd->ndom; ++d) {
+        if (!a[d] || !b[d]) return set_error(WL_ERR_ARG, "NULL block field");
+        loc[d] = dd->loc + (size_t)3 * nrhs * d;
+        WL_TRY(launch_cdot(dd->dom[d], prec, a[d], b[d], 1, nrhs, loc[d], 3, nullptr, s));
+    }
+    outs[0] = out;
+    return dd_allreduce(dd, loc, outs, 3, nrhs, nullptr, 1, s);
+}

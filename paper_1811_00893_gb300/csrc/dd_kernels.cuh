@@ -1,0 +1,161 @@
+// Kernels of the domain-decomposed hopping term (dd.cuh): face packing,
+// interior and boundary sweeps, and the sum over the blocks.  Templates over
+// precision P, dagger DAG, fused reduction DOT, link format LF and the site
+// set (BND: boundary sites, whose hops may read the halo).  dd_hop.cu
+// instantiates LF = 0 (all nine entries per link), dd_hop_r12.cu LF = 1
+// (two-row compressed links), so the two compile in parallel.
+#pragma once
+
+#include "dd.cuh"
+#include "hop_kernels.cuh"
+
+namespace wl {
+
+static constexpr int kDDBlock = 128;
+
+template <int P, bool DAG, bool DOT, int LF, bool BND>
+__global__ void __launch_bounds__(kDDBlock, (MinBlocks<P, DOT>::value * 2)) dd_hop_kernel(const DDArgs A)
+{
+    using T = typename Prec<P>::real;
+    const int rhs = blockIdx.y, dom = blockIdx.z;
+    const DDDom& D = A.d[dom];
+    if (D.active && D.active[(long long)rhs * A.active_stride] == 0) return;  // uniform per block
+    const int pidx = blockIdx.x / A.blocks_per_parity;
+    const long long j = (long long)(blockIdx.x - pidx * A.blocks_per_parity) * kDDBlock + threadIdx.x;
+    T part[3] = {0, 0, 0};
+    if (j < A.nsites) {
+        const int i = A.sites[j];
+        const int p = A.parity0 + pidx;
+        int c[4], xh, nb[8];
+        half_coords(A.g, p, i, c, xh);
+        const unsigned faces = block_neighbours(A.g, i, c, xh, nb);
+        const unsigned cross = faces & D.edge;  // hops that cross the global boundary
+        const char* halo[4][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+        long long f[4] = {0, 0, 0, 0};
+        unsigned remote = 0;
+        if constexpr (BND) {
+            remote = faces & A.cutmask;
+#pragma unroll
+            for (int mu = 1; mu < 4; ++mu)
+                if (A.fs[mu]) {
+                    f[mu] = face_index(A.g, mu, c, xh);
+                    const long long seg_rs = A.fs[mu] * (long long)(16 * halo_planes(P));
+                    halo[mu][0] = D.halo + A.hoff[pidx][mu][0] + rhs * seg_rs;
+                    halo[mu][1] = D.halo + A.hoff[pidx][mu][1] + rhs * seg_rs;
+                }
+        }
+        cx<T> acc[12];
+        dd_hop_site<P, DAG, LF, BND>(acc, A, D.in[pidx] + rhs * A.rs_in, D.links[pidx], i, nb, cross, remote, halo, f);
+        auto at = [&](const char* q, long long rs) -> const char* { return q ? q + rhs * rs : nullptr; };
+        epilogue_ptrs<P, DOT, kClNone>(acc, A.a, at(D.x1[pidx], A.rs_x1), at(D.x2[pidx], A.rs_x2), A.b1,
+                                       at(D.w[pidx], A.rs_w), D.out[pidx] + rhs * A.rs_out, A.g.Vh, i, part);
+    }
+    if constexpr (DOT) {
+        typename RedType<T>::type wp[3] = {(typename RedType<T>::type)part[0], (typename RedType<T>::type)part[1],
+                                           (typename RedType<T>::type)part[2]};
+        warp_sum<3>(wp);
+        double bp[3] = {(double)wp[0], (double)wp[1], (double)wp[2]};
+        __shared__ double sh[3 * 32];
+        block_sum_warps<3>(bp, sh);
+        if (threadIdx.x == 0) {
+            double* o = A.partial + dom * A.dom_stride + ((long long)rhs * A.max_blocks + A.block0 + blockIdx.x) * 3;
+            o[0] = bp[0];
+            o[1] = bp[1];
+            o[2] = bp[2];
+        }
+    }
+}
+
+// The spin-projected half spinors of the faces a neighbouring block needs.
+template <int P, bool DAG>
+__global__ void __launch_bounds__(kDDBlock) dd_pack_kernel(const DDPackArgs A)
+{
+    using T = typename Prec<P>::real;
+    const int rhs = blockIdx.y, dom = blockIdx.z;
+    const long long j = blockIdx.x * (long long)kDDBlock + threadIdx.x;
+    if (j >= A.total) return;
+    int k = 0;
+    while (k + 1 < A.nseg && j >= A.seg[k + 1].start) ++k;
+    const DDSeg& S = A.seg[k];
+    const long long f = j - S.start;
+    // face index -> half index at x_mu = 0 (side 0) or L_mu - 1 (side 1)
+    const long long s_mu = S.mu == 1 ? A.g.sy : S.mu == 2 ? A.g.sz : A.g.st;
+    const long long above = f / s_mu, below = f - above * s_mu;
+    const long long xmu = S.side ? A.g.L[S.mu] - 1 : 0;
+    const int i = (int)(below + xmu * s_mu + above * s_mu * A.g.L[S.mu]);
+    const char* in = A.in[dom][S.pidx] + rhs * A.rs_in;
+    cx<T> h0[3], h1[3];
+    const int d = 2 * S.mu + S.side;  // the hop of the receiving block
+    if constexpr (P == WL_DF64) {
+        cx<T> q[12];
+        load_spinor_ro<P>(q, in, A.g.Vh, i);
+        project_loop<P, DAG>(h0, h1, q, d);
+    } else {
+        constexpr int F = DAG ? +1 : -1;  // forward projector sign
+        constexpr int B = -F;
+        switch (d) {
+            case 2: load_project<P, 1, F>(h0, h1, in, A.g.Vh, i); break;
+            case 3: load_project<P, 1, B>(h0, h1, in, A.g.Vh, i); break;
+            case 4: load_project<P, 2, F>(h0, h1, in, A.g.Vh, i); break;
+            case 5: load_project<P, 2, B>(h0, h1, in, A.g.Vh, i); break;
+            case 6: load_project<P, 3, F>(h0, h1, in, A.g.Vh, i); break;
+            default: load_project<P, 3, B>(h0, h1, in, A.g.Vh, i); break;
+        }
+    }
+    const long long seg_rs = S.count * (long long)(16 * halo_planes(P));
+    store_half<P>(A.dst[dom][S.mu][S.side] + A.hoff[S.pidx][S.mu][S.side] + rhs * seg_rs, S.count, f, h0, h1);
+}
+
+// Launchers of one link format (LF = 1 exists for FP32 / FP16 only).
+template <int LF>
+struct DDKernels {
+    static void hop(int prec, bool dagger, bool dot, bool bnd, const DDArgs& A, dim3 grid, cudaStream_t s);
+    static void pack(int prec, bool dagger, const DDPackArgs& A, dim3 grid, cudaStream_t s);
+};
+
+template <int LF, int P, bool BND>
+static void dd_hop_p(bool dagger, bool dot, const DDArgs& A, dim3 grid, cudaStream_t s)
+{
+    if (dagger) {
+        if (dot) dd_hop_kernel<P, true, true, LF, BND><<<grid, kDDBlock, 0, s>>>(A);
+        else dd_hop_kernel<P, true, false, LF, BND><<<grid, kDDBlock, 0, s>>>(A);
+    } else {
+        if (dot) dd_hop_kernel<P, false, true, LF, BND><<<grid, kDDBlock, 0, s>>>(A);
+        else dd_hop_kernel<P, false, false, LF, BND><<<grid, kDDBlock, 0, s>>>(A);
+    }
+}
+
+template <int LF, int P>
+static void dd_hop_pb(bool dagger, bool dot, bool bnd, const DDArgs& A, dim3 grid, cudaStream_t s)
+{
+    if (bnd) dd_hop_p<LF, P, true>(dagger, dot, A, grid, s);
+    else dd_hop_p<LF, P, false>(dagger, dot, A, grid, s);
+}
+
+template <int LF>
+void DDKernels<LF>::hop(int prec, bool dagger, bool dot, bool bnd, const DDArgs& A, dim3 grid, cudaStream_t s)
+{
+    if (prec == WL_F32) dd_hop_pb<LF, WL_F32>(dagger, dot, bnd, A, grid, s);
+    else if (prec == WL_F16) dd_hop_pb<LF, WL_F16>(dagger, dot, bnd, A, grid, s);
+    else if constexpr (LF == 0) {
+        if (prec == WL_F64) dd_hop_pb<LF, WL_F64>(dagger, dot, bnd, A, grid, s);
+        else dd_hop_pb<LF, WL_DF64>(dagger, dot, bnd, A, grid, s);
+    }
+}
+
+template <int LF>
+void DDKernels<LF>::pack(int prec, bool dagger, const DDPackArgs& A, dim3 grid, cudaStream_t s)
+{
+    // the packed half spinor does not depend on the link format
+    auto go = [&](auto pc) {
+        constexpr int PP = decltype(pc)::value;
+        if (dagger) dd_pack_kernel<PP, true><<<grid, kDDBlock, 0, s>>>(A);
+        else dd_pack_kernel<PP, false><<<grid, kDDBlock, 0, s>>>(A);
+    };
+    if (prec == WL_F32) go(std::integral_constant<int, WL_F32>());
+    else if (prec == WL_F16) go(std::integral_constant<int, WL_F16>());
+    else if (prec == WL_F64) go(std::integral_constant<int, WL_F64>());
+    else go(std::integral_constant<int, WL_DF64>());
+}
+
+}  // namespace wl

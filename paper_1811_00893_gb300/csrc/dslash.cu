@@ -317,6 +317,7 @@ using namespace wl;
 static int check_common(wl_gauge g, const void* out, const void* in, wl_prec prec, int nrhs)
 {
     if (!g) return set_error(WL_ERR_ARG, "NULL gauge object");
+    if (g->dd_part) return set_error(WL_ERR_STATE, "block of a domain decomposition: use the _dd calls");
     if (prec < WL_F64 || prec > WL_DF64) return set_error(WL_ERR_ARG, "unknown precision");
     if (nrhs < 1) return set_error(WL_ERR_ARG, "nrhs must be >= 1");
     if (nrhs > 65535) return set_error(WL_ERR_ARG, "nrhs must be <= 65535");

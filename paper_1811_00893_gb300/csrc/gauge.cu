@@ -113,33 +113,54 @@ struct BC {
     double re[4], im[4];
 };
 
+// Where a gauge object's sites sit in the lattice its links come from: the
+// whole lattice (origin 0, gl = the object's own geometry), or one block of a
+// domain decomposition (gl = the global lattice, origin = the block's first
+// site).  Links are read from the global field at global coordinates, so the
+// hop matrices of a block's face sites are those of the undivided lattice:
+// neighbours across a cut face and boundary phases come from the global
+// geometry.
+struct Place {
+    Geom gl;
+    int o[4];
+};
+
+// Global site index of half site i (parity p of the local lattice) and its
+// global coordinates.
+__device__ __forceinline__ long long global_site(const Geom& g, const Place& pl, int p, long long i,
+                                                 int (&c)[4])
+{
+    long long r = site_of_half(g, p, i);
+    for (int mu = 0; mu < 4; ++mu) {
+        c[mu] = (int)(r % g.L[mu]) + pl.o[mu];
+        r /= g.L[mu];
+    }
+    return c[0] + (long long)pl.gl.L[0] * (c[1] + (long long)pl.gl.L[1] * (c[2] + (long long)pl.gl.L[2] * c[3]));
+}
+
 template <int P>
-__global__ void build_links_kernel(void* out, const double* __restrict__ U, Geom g, BC bc, int p)
+__global__ void build_links_kernel(void* out, const double* __restrict__ U, Geom g, Place pl, BC bc, int p)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= g.Vh) return;
-    const long long s = site_of_half(g, p, i);
     int c[4];
-    long long r = s;
-    for (int mu = 0; mu < 4; ++mu) {
-        c[mu] = (int)(r % g.L[mu]);
-        r /= g.L[mu];
-    }
-    const long long stride[4] = {1, g.L[0], (long long)g.L[0] * g.L[1],
-                                 (long long)g.L[0] * g.L[1] * g.L[2]};
+    const long long s = global_site(g, pl, p, i, c);
+    const Geom& G = pl.gl;
+    const long long stride[4] = {1, G.L[0], (long long)G.L[0] * G.L[1],
+                                 (long long)G.L[0] * G.L[1] * G.L[2]};
     for (int mu = 0; mu < 4; ++mu) {
         cx<double> w[9];
         // forward: phi^[x_mu = L-1] U_mu(x)
         const double* u = U + (s * 4 + mu) * 18;
         double pr = 1.0, pi = 0.0;
-        if (c[mu] == g.L[mu] - 1) { pr = bc.re[mu]; pi = bc.im[mu]; }
+        if (c[mu] == G.L[mu] - 1) { pr = bc.re[mu]; pi = bc.im[mu]; }
         for (int k = 0; k < 9; ++k) {
             const double a = u[2 * k], b = u[2 * k + 1];
             w[k] = {pr * a - pi * b, pr * b + pi * a};
         }
         store_link<P>(out, g.Vh, 2 * mu, i, w);
         // backward: conj(phi)^[x_mu = 0] U_mu(x - mu)^dag
-        const long long n = (c[mu] == 0) ? s + (g.L[mu] - 1) * stride[mu] : s - stride[mu];
+        const long long n = (c[mu] == 0) ? s + (G.L[mu] - 1) * stride[mu] : s - stride[mu];
         const double* v = U + (n * 4 + mu) * 18;
         pr = 1.0;
         pi = 0.0;
@@ -203,26 +224,23 @@ __device__ double su3_deviation(const double* u)
 }
 
 template <int P>
-__global__ void build_links_r12_kernel(void* out, const double* __restrict__ U, Geom g, int p, int* flag)
+__global__ void build_links_r12_kernel(void* out, const double* __restrict__ U, Geom g, Place pl, int p,
+                                       int* flag)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= g.Vh) return;
-    const long long s = site_of_half(g, p, i);
     int c[4];
-    long long r = s;
-    for (int mu = 0; mu < 4; ++mu) {
-        c[mu] = (int)(r % g.L[mu]);
-        r /= g.L[mu];
-    }
-    const long long stride[4] = {1, g.L[0], (long long)g.L[0] * g.L[1],
-                                 (long long)g.L[0] * g.L[1] * g.L[2]};
+    const long long s = global_site(g, pl, p, i, c);
+    const Geom& G = pl.gl;
+    const long long stride[4] = {1, G.L[0], (long long)G.L[0] * G.L[1],
+                                 (long long)G.L[0] * G.L[1] * G.L[2]};
     for (int mu = 0; mu < 4; ++mu) {
         cx<double> w[9];
         const double* u = U + (s * 4 + mu) * 18;
         if (su3_deviation(u) > 1e-6) atomicOr(flag, 1);
         for (int k = 0; k < 9; ++k) w[k] = {u[2 * k], u[2 * k + 1]};
         store_link_r12<P>(out, g.Vh, 2 * mu, i, w);
-        const long long n = (c[mu] == 0) ? s + (g.L[mu] - 1) * stride[mu] : s - stride[mu];
+        const long long n = (c[mu] == 0) ? s + (G.L[mu] - 1) * stride[mu] : s - stride[mu];
         const double* v = U + (n * 4 + mu) * 18;
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) w[a * 3 + b] = {v[2 * (b * 3 + a)], -v[2 * (b * 3 + a) + 1]};
@@ -330,46 +348,31 @@ void timing_end(wl_gauge g, cudaStream_t s, int slot)
 
 using namespace wl;
 
-static int validate_lattice(const wl_lattice* lat)
-{
-    if (!lat) return set_error(WL_ERR_ARG, "NULL lattice");
-    long long V = 1;
-    for (int k = 0; k < 4; ++k) {
-        if (lat->dims[k] < 2 || lat->dims[k] % 2)
-            return set_error(WL_ERR_ARG, "lattice extents must be even and >= 2");
-        V *= lat->dims[k];
-    }
-    if (V / 2 > 0x7fffffffLL / 16)
-        return set_error(WL_ERR_ARG, "lattice too large for 32-bit half-index arithmetic");
-    for (int k = 0; k < 4; ++k) {
-        const double m = std::hypot(lat->bc_re[k], lat->bc_im[k]);
-        if (std::fabs(m - 1.0) > 1e-12) return set_error(WL_ERR_ARG, "boundary phases must have |phi| = 1");
-    }
-    if (!std::isfinite(lat->kappa)) return set_error(WL_ERR_ARG, "kappa must be finite");
-    return WL_OK;
-}
+namespace wl {
 
-extern "C" int wl_gauge_create(wl_gauge* out, const wl_lattice* lat, const double* U, int prec_mask,
-                               void* stream)
+// Create a gauge object for the local lattice `local` whose links are read
+// from the canonical field U of the lattice `global` (equal to `local` for an
+// undivided lattice) at the block starting at `origin`.
+int gauge_create(wl_gauge* out, const wl_lattice* local, const wl_lattice* global, const int* origin,
+                 const double* U, int prec_mask, cudaStream_t s)
 {
-    WL_ENTRY();
-    if (!out) return set_error(WL_ERR_ARG, "NULL output handle");
     *out = nullptr;
-    WL_TRY(validate_lattice(lat));
     if (!U) return set_error(WL_ERR_ARG, "NULL gauge field");
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, U) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
         cudaGetLastError();
         return set_error(WL_ERR_ARG, "gauge field must be device memory");
     }
-    cudaStream_t s = (cudaStream_t)stream;
     auto g = new wl_gauge_s();
-    g->geo = make_geom(lat->dims);
-    g->kappa = lat->kappa;
+    g->geo = make_geom(local->dims);
+    g->kappa = local->kappa;
     for (int k = 0; k < 4; ++k) {
-        g->bc_re[k] = lat->bc_re[k];
-        g->bc_im[k] = lat->bc_im[k];
+        g->bc_re[k] = local->bc_re[k];
+        g->bc_im[k] = local->bc_im[k];
     }
+    Place pl;
+    pl.gl = make_geom(global->dims);
+    for (int k = 0; k < 4; ++k) pl.o[k] = origin ? origin[k] : 0;
     g->prec_mask = (prec_mask & WL_PREC_ALL) | WL_PREC_MASK(WL_F64);
     // the outer residual corrections of mixed-precision solves run in df64
     if (g->prec_mask & (WL_PREC_MASK(WL_F32) | WL_PREC_MASK(WL_F16)))
@@ -380,8 +383,8 @@ extern "C" int wl_gauge_create(wl_gauge* out, const wl_lattice* lat, const doubl
         cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
         BC bc;
         for (int k = 0; k < 4; ++k) {
-            bc.re[k] = lat->bc_re[k];
-            bc.im[k] = lat->bc_im[k];
+            bc.re[k] = global->bc_re[k];
+            bc.im[k] = global->bc_im[k];
         }
         const int block = 128;
         const unsigned grid = (unsigned)((g->geo.Vh + block - 1) / block);
@@ -393,10 +396,10 @@ extern "C" int wl_gauge_create(wl_gauge* out, const wl_lattice* lat, const doubl
                     rc = set_error(WL_ERR_CUDA, std::string("cudaMalloc links: ") + cudaGetErrorString(e));
                     break;
                 }
-                if (prec == WL_F64) build_links_kernel<WL_F64><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, bc, p);
-                else if (prec == WL_F32) build_links_kernel<WL_F32><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, bc, p);
-                else if (prec == WL_F16) build_links_kernel<WL_F16><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, bc, p);
-                else build_links_kernel<WL_DF64><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, bc, p);
+                if (prec == WL_F64) build_links_kernel<WL_F64><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, pl, bc, p);
+                else if (prec == WL_F32) build_links_kernel<WL_F32><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, pl, bc, p);
+                else if (prec == WL_F16) build_links_kernel<WL_F16><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, pl, bc, p);
+                else build_links_kernel<WL_DF64><<<grid, block, 0, s>>>(g->links[prec][p], U, g->geo, pl, bc, p);
                 e = cudaGetLastError();
                 if (e != cudaSuccess) {
                     rc = set_error(WL_ERR_CUDA, std::string("link build launch: ") + cudaGetErrorString(e));
@@ -424,8 +427,8 @@ extern "C" int wl_gauge_create(wl_gauge* out, const wl_lattice* lat, const doubl
                         rc = set_error(WL_ERR_CUDA, "cudaMalloc compressed links");
                         break;
                     }
-                    if (prec == WL_F32) build_links_r12_kernel<WL_F32><<<grid, block, 0, s>>>(g->links_r12[prec][p], U, g->geo, p, flag);
-                    else build_links_r12_kernel<WL_F16><<<grid, block, 0, s>>>(g->links_r12[prec][p], U, g->geo, p, flag);
+                    if (prec == WL_F32) build_links_r12_kernel<WL_F32><<<grid, block, 0, s>>>(g->links_r12[prec][p], U, g->geo, pl, p, flag);
+                    else build_links_r12_kernel<WL_F16><<<grid, block, 0, s>>>(g->links_r12[prec][p], U, g->geo, pl, p, flag);
                     if (cudaGetLastError() != cudaSuccess) rc = set_error(WL_ERR_CUDA, "compressed link build launch");
                     count_launch(1, (double)g->geo.Vh * (8 * 144.0 + bytes / g->geo.Vh));
                 }
@@ -448,6 +451,37 @@ extern "C" int wl_gauge_create(wl_gauge* out, const wl_lattice* lat, const doubl
     }
     *out = g;
     return WL_OK;
+}
+
+int validate_lattice(const wl_lattice* lat)
+{
+    if (!lat) return set_error(WL_ERR_ARG, "NULL lattice");
+    long long V = 1;
+    for (int k = 0; k < 4; ++k) {
+        if (lat->dims[k] < 2 || lat->dims[k] % 2)
+            return set_error(WL_ERR_ARG, "lattice extents must be even and >= 2");
+        V *= lat->dims[k];
+    }
+    if (V / 2 > 0x7fffffffLL / 16)
+        return set_error(WL_ERR_ARG, "lattice too large for 32-bit half-index arithmetic");
+    for (int k = 0; k < 4; ++k) {
+        const double m = std::hypot(lat->bc_re[k], lat->bc_im[k]);
+        if (std::fabs(m - 1.0) > 1e-12) return set_error(WL_ERR_ARG, "boundary phases must have |phi| = 1");
+    }
+    if (!std::isfinite(lat->kappa)) return set_error(WL_ERR_ARG, "kappa must be finite");
+    return WL_OK;
+}
+
+}  // namespace wl
+
+extern "C" int wl_gauge_create(wl_gauge* out, const wl_lattice* lat, const double* U, int prec_mask,
+                               void* stream)
+{
+    WL_ENTRY();
+    if (!out) return set_error(WL_ERR_ARG, "NULL output handle");
+    *out = nullptr;
+    WL_TRY(validate_lattice(lat));
+    return gauge_create(out, lat, lat, nullptr, U, prec_mask, (cudaStream_t)stream);
 }
 
 void free_workspace(wl_gauge g);  // solver.cu

@@ -464,6 +464,49 @@ __device__ __forceinline__ void hop_one(cx<typename Prec<P>::real> (&acc)[12], c
     }
 }
 
+// The part of hop_one after the spin projection: given the projected half
+// spinor (h0, h1) of hop D, apply the boundary phase (compressed links), the
+// link and the reconstruction.  The domain-decomposed kernels use it for hops
+// whose half spinor arrives from a neighbouring block, and with load_project
+// for the others; it performs the same operations as hop_one.
+template <int P, int D, int MU, int S, int LF>
+__device__ __forceinline__ void hop_apply(cx<typename Prec<P>::real> (&acc)[12], cx<typename Prec<P>::real> (&h0)[3],
+                                          cx<typename Prec<P>::real> (&h1)[3], const void* links, long long lVh,
+                                          long long li, unsigned cross, const cx<float>* ph)
+{
+    using T = typename Prec<P>::real;
+    if constexpr (LF == 1) {
+        if (cross & (1u << D)) {
+            const cx<T> f = (D & 1) ? conj(ph[MU]) : ph[MU];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                h0[c] = f * h0[c];
+                h1[c] = f * h1[c];
+            }
+        }
+        cx<T> W[9];
+        load_link_r12<P>(W, links, lVh, D, li);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            reconstruct<MU, S>(acc, a, dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h0),
+                               dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h1));
+    } else if constexpr (P == WL_F64) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cx<T> w[3];
+            load_link_row<P>(w, links, lVh, D, li, a);
+            reconstruct<MU, S>(acc, a, dot3(w[0], w[1], w[2], h0), dot3(w[0], w[1], w[2], h1));
+        }
+    } else {
+        cx<T> W[9];
+        load_link<P>(W, links, lVh, D, li);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            reconstruct<MU, S>(acc, a, dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h0),
+                               dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h1));
+    }
+}
+
 // i^k x for k = 0..3 (multiplication by 1, i, -1, -i: swaps and negations,
 // exact in every arithmetic type)
 template <typename T>

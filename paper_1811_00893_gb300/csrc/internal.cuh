@@ -67,11 +67,20 @@ struct wl_gauge_s {
     void* clov[4][2][2] = {};
     bool has_clover = false;
     std::map<std::string, wl::Tuned> tuned;
+    // set for a block of a domain decomposition (wl_dd): its links see the
+    // neighbouring blocks across the cut faces, so only the _dd calls apply it
+    int dd_part = 0;
 };
 
 namespace wl {
 
 Geom make_geom(const int* dims);
+int validate_lattice(const wl_lattice* lat);
+// Gauge object of the lattice `local`, its links read from the canonical field
+// U of the lattice `global` at the block that starts at `origin` (nullptr:
+// the undivided lattice, global = local).
+int gauge_create(wl_gauge* out, const wl_lattice* local, const wl_lattice* global, const int* origin,
+                 const double* U, int prec_mask, cudaStream_t s);
 
 // Canonical (x-fastest) site index of half-site i of parity p: the half
 // index runs over x/2 fastest, then y, z, t; the site's parity fixes x's

@@ -15,8 +15,6 @@
 // atomics are used, and the result is deterministic.  The array is shared by
 // all calls: calls that overlap on the GPU (different streams, or different
 // host threads on one device without ordering) race on it.
-#include <mutex>
-
 #include "internal.cuh"
 
 namespace wl {
@@ -50,9 +48,9 @@ __global__ void __launch_bounds__(kNaThreads) na_partial_kernel(const char* a, c
             ci = fma(x[c].re, y[c].im, fma(-x[c].im, y[c].re, ci));
             nn = fma(y[c].re, y[c].re, fma(y[c].im, y[c].im, nn));
         }
-        part[0] += cr;
-        part[1] += ci;
-        part[2] += nn;
+        part[0] += (double)cr;
+        part[1] += (double)ci;
+        part[2] += (double)nn;
     }
     __shared__ double sh[3 * 32];
     block_sum<3>(part, sh);
@@ -77,22 +75,15 @@ __global__ void __launch_bounds__(kNaThreads) na_finish_kernel(const double* par
         for (int k = 0; k < 3; ++k) out[3 * rhs + k] = v[k];
 }
 
-// Device address of na_partial on the current device, looked up once per
-// device (the host-side symbol is only a stand-in for it).
+// Device address of na_partial in the current device's context.  The
+// host-side symbol is only a stand-in for it, so the address is looked up on
+// every call (a host-side query; cheap once the module is loaded): a context
+// that was reset and re-created (cudaDeviceReset) gets the new address.
 static int na_scratch(double** ptr)
 {
-    static std::mutex mu;
-    static double* addr[64] = {};
-    int dev = 0;
-    WL_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return set_error(WL_ERR_CUDA, "device ordinal out of range");
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void* p = nullptr;
-        WL_CUDA(cudaGetSymbolAddress(&p, na_partial));
-        addr[dev] = (double*)p;
-    }
-    *ptr = addr[dev];
+    void* p = nullptr;
+    WL_CUDA(cudaGetSymbolAddress(&p, na_partial));
+    *ptr = (double*)p;
     return WL_OK;
 }
 
@@ -103,12 +94,13 @@ using namespace wl;
 extern "C" int wl_cdot_noalloc(double* out, const void* a, const void* b, long long Vh,
                                wl_prec prec, int nrhs, void* stream)
 {
+    WL_ENTRY();
     if (!out || !a || !b) return set_error(WL_ERR_ARG, "NULL pointer");
-    if (prec < WL_F64 || prec > WL_F16) return set_error(WL_ERR_ARG, "unknown precision");
+    if (prec < WL_F64 || prec > WL_DF64) return set_error(WL_ERR_ARG, "unknown precision");
     if (Vh < 1) return set_error(WL_ERR_ARG, "Vh must be >= 1");
     if (nrhs < 1 || nrhs > kNaMaxRhs)
         return set_error(WL_ERR_ARG, "nrhs must be in 1..WL_NOALLOC_MAX_RHS (64) for wl_cdot_noalloc");
-    if (prec == WL_F16 && Vh % 4)
+    if (prec == WL_F16 && Vh % 4)  // 52 Vh bytes per field: 16-byte rows of the next field
         return set_error(WL_ERR_ARG, "FP16 fields need Vh divisible by 4");
     double* partial = nullptr;
     WL_TRY(na_scratch(&partial));
@@ -121,8 +113,10 @@ extern "C" int wl_cdot_noalloc(double* out, const void* a, const void* b, long l
         na_partial_kernel<WL_F64><<<grid, kNaThreads, 0, s>>>((const char*)a, (const char*)b, Vh, fb, partial);
     else if (prec == WL_F32)
         na_partial_kernel<WL_F32><<<grid, kNaThreads, 0, s>>>((const char*)a, (const char*)b, Vh, fb, partial);
-    else
+    else if (prec == WL_F16)
         na_partial_kernel<WL_F16><<<grid, kNaThreads, 0, s>>>((const char*)a, (const char*)b, Vh, fb, partial);
+    else
+        na_partial_kernel<WL_DF64><<<grid, kNaThreads, 0, s>>>((const char*)a, (const char*)b, Vh, fb, partial);
     WL_CHECK_LAUNCH(2.0 * fb * nrhs);
     na_finish_kernel<<<nrhs, kNaThreads, 0, s>>>(partial, nb, out);
     WL_CHECK_LAUNCH(0.0);

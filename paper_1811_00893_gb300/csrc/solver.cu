@@ -690,6 +690,7 @@ static int check_params(wl_gauge g, const void* x, const void* b, int nrhs,
                         const wl_solve_params* prm)
 {
     if (!g) return set_error(WL_ERR_ARG, "NULL gauge object");
+    if (g->dd_part) return set_error(WL_ERR_STATE, "block of a domain decomposition: use the _dd calls");
     if (!x || !b || !prm) return set_error(WL_ERR_ARG, "NULL pointer");
     if (nrhs < 1 || nrhs > 65535) return set_error(WL_ERR_ARG, "nrhs must be in 1..65535");
     if (prm->inner < WL_F64 || prm->inner > WL_F16) return set_error(WL_ERR_ARG, "unknown inner precision");

@@ -20,9 +20,9 @@ from . import build as _build
 WL_F64, WL_F32, WL_F16, WL_DF64 = 0, 1, 2, 3
 PREC = {"f64": WL_F64, "f32": WL_F32, "f16": WL_F16, "df64": WL_DF64}
 WL_OK, WL_ERR_ARG, WL_ERR_CUDA, WL_ERR_NOT_CONVERGED = 0, -1, -2, -3
-WL_ERR_BREAKDOWN, WL_ERR_NAN, WL_ERR_TIMEOUT, WL_ERR_STATE = -4, -5, -6, -7
+WL_ERR_BREAKDOWN, WL_ERR_NAN, WL_ERR_STATE = -4, -5, -7
 ERR_NAMES = {0: "WL_OK", -1: "WL_ERR_ARG", -2: "WL_ERR_CUDA", -3: "WL_ERR_NOT_CONVERGED",
-             -4: "WL_ERR_BREAKDOWN", -5: "WL_ERR_NAN", -6: "WL_ERR_TIMEOUT", -7: "WL_ERR_STATE"}
+             -4: "WL_ERR_BREAKDOWN", -5: "WL_ERR_NAN", -7: "WL_ERR_STATE"}
 
 
 #: wl_gauge_create flag: also keep two-row (reconstruct-12) FP32/FP16 links
@@ -95,6 +95,18 @@ def load() -> ctypes.CDLL:
                                  ctypes.POINTER(wl_solve_info), P]),
             "wilson_solve_batch": (I, [I, P, P, P, P, ctypes.POINTER(wl_solve_params),
                                        ctypes.POINTER(wl_solve_info), P]),
+            "wl_dd_create": (I, [ctypes.POINTER(P), ctypes.POINTER(wl_lattice), ctypes.POINTER(I), P, I, P]),
+            "wl_dd_destroy": (I, [P]),
+            "wl_dd_blocks": (I, [P]),
+            "wl_dd_block": (I, [P, I, ctypes.POINTER(P), ctypes.POINTER(I)]),
+            "wl_dd_set_exchange": (I, [P, I]),
+            "wl_dd_scatter": (I, [P, P, P, I, P]),
+            "wl_dd_gather": (I, [P, P, P, I, P]),
+            "wilson_dslash_dd": (I, [P, P, P, I, I, I, I, P]),
+            "wilson_mult_dd": (I, [P, P, P, I, I, I, I, P]),
+            "wl_cdot_dd": (I, [P, P, P, P, I, I, P]),
+            "wilson_solve_dd": (I, [P, P, P, I, ctypes.POINTER(wl_solve_params),
+                                    ctypes.POINTER(wl_solve_info), P]),
             "wl_last_error": (ctypes.c_char_p, []),
             "wl_spinor16_format": (I, []),
             "wl_launch_count": (LL, []),
@@ -114,7 +126,10 @@ def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["wl_gauge_create", "wl_gauge_destroy", "wl_half_volume", "wl_field_bytes",
             "wl_field_to_internal", "wl_field_to_canonical", "wilson_dslash", "wilson_mult",
-            "wl_clover_set", "wl_clover_apply", "wl_cdot", "wl_cdot_noalloc", "wilson_solve", "wilson_solve_batch", "wl_last_error",
+            "wl_clover_set", "wl_clover_apply", "wl_cdot", "wl_cdot_noalloc", "wilson_solve",
+            "wilson_solve_batch", "wl_dd_create", "wl_dd_destroy", "wl_dd_blocks", "wl_dd_block",
+            "wl_dd_set_exchange", "wl_dd_scatter", "wl_dd_gather", "wilson_dslash_dd",
+            "wilson_mult_dd", "wl_cdot_dd", "wilson_solve_dd", "wl_last_error",
             "wl_spinor16_format",
             "wl_launch_count", "wl_algorithmic_bytes", "wl_timing", "wl_timing_read"]
 
@@ -255,6 +270,76 @@ def wilson_solve_batch(gs, xs, bs, nrhs, params: wl_solve_params, stream=None, c
     return rc, _infos(info, total)
 
 
+# ---------------------------------------------------------------------------
+# domain decomposition (block fields are passed as lists, one per block)
+# ---------------------------------------------------------------------------
+
+def _ptrs(ts):
+    return (ctypes.c_void_p * len(ts))(*[_ptr(t).value for t in ts])
+
+
+def wl_dd_create(lat: wl_lattice, grid, U: torch.Tensor, mask: int, stream=None) -> ctypes.c_void_p:
+    dd = ctypes.c_void_p()
+    G = (ctypes.c_int * 4)(*[int(k) for k in grid])
+    _check(load().wl_dd_create(ctypes.byref(dd), ctypes.byref(lat), G, _ptr(U), int(mask),
+                               _stream(stream)))
+    return dd
+
+
+def wl_dd_destroy(dd) -> None:
+    _check(load().wl_dd_destroy(dd))
+
+
+def wl_dd_blocks(dd) -> int:
+    return int(load().wl_dd_blocks(dd))
+
+
+def wl_dd_block(dd, k: int):
+    """(gauge handle, grid coordinates) of block k."""
+    g = ctypes.c_void_p()
+    c = (ctypes.c_int * 4)()
+    _check(load().wl_dd_block(dd, int(k), ctypes.byref(g), c))
+    return g, tuple(c)
+
+
+def wl_dd_set_exchange(dd, mode: int) -> None:
+    _check(load().wl_dd_set_exchange(dd, int(mode)))
+
+
+def wl_dd_scatter(dd, local, glob, nrhs: int, stream=None) -> None:
+    _check(load().wl_dd_scatter(dd, _ptrs(local), _ptr(glob), int(nrhs), _stream(stream)))
+
+
+def wl_dd_gather(dd, glob, local, nrhs: int, stream=None) -> None:
+    _check(load().wl_dd_gather(dd, _ptr(glob), _ptrs(local), int(nrhs), _stream(stream)))
+
+
+def wilson_dslash_dd(dd, out, inp, out_parity: int, dagger: int, prec: int, nrhs: int,
+                     stream=None) -> None:
+    _check(load().wilson_dslash_dd(dd, _ptrs(out), _ptrs(inp), int(out_parity), int(dagger),
+                                   int(prec), int(nrhs), _stream(stream)))
+
+
+def wilson_mult_dd(dd, out, inp, eo: int, dagger: int, prec: int, nrhs: int, stream=None) -> None:
+    _check(load().wilson_mult_dd(dd, _ptrs(out), _ptrs(inp), int(eo), int(dagger), int(prec),
+                                 int(nrhs), _stream(stream)))
+
+
+def wl_cdot_dd(dd, out, a, b, prec: int, nrhs: int, stream=None) -> None:
+    _check(load().wl_cdot_dd(dd, _ptr(out), _ptrs(a), _ptrs(b), int(prec), int(nrhs),
+                             _stream(stream)))
+
+
+def wilson_solve_dd(dd, xs, bs, nrhs: int, params: wl_solve_params, stream=None, check=True):
+    """Returns (status, [info per rhs]); xs, bs: block-local canonical fields."""
+    info = (wl_solve_info * nrhs)()
+    rc = load().wilson_solve_dd(dd, _ptrs(xs), _ptrs(bs), int(nrhs), ctypes.byref(params), info,
+                                _stream(stream))
+    if check:
+        _check(rc)
+    return rc, _infos(info, nrhs)
+
+
 def wl_last_error() -> str:
     return load().wl_last_error().decode()
 
@@ -308,6 +393,53 @@ class Gauge:
     def close(self):
         if self.handle is not None:
             wl_gauge_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Decomposition:
+    """Owns a wl_dd handle: the lattice `dims` cut into `grid` blocks."""
+
+    def __init__(self, dims, kappa, U: torch.Tensor, grid, precs=("f64", "f32", "f16"),
+                 bc=(1, 1, 1, -1), stream=None, r12: bool = False):
+        self.dims = tuple(int(d) for d in dims)
+        self.grid = tuple(int(k) for k in grid)
+        self.kappa = float(kappa)
+        self.lat = lattice(dims, kappa, bc)
+        mask = prec_mask(*precs) | (WL_LINKS_R12 if r12 else 0)
+        self.handle = wl_dd_create(self.lat, self.grid, U, mask, stream)
+        self.n = wl_dd_blocks(self.handle)
+        self.blocks = [wl_dd_block(self.handle, k) for k in range(self.n)]
+        self.local_dims = tuple(self.dims[m] // self.grid[m] for m in range(4))
+        self.Vh = wl_half_volume(self.blocks[0][0])
+
+    def field(self, prec, nrhs: int = 1, nhalf: int = 1):
+        """One internal field per block."""
+        p = PREC[prec] if isinstance(prec, str) else prec
+        n = wl_field_bytes(self.blocks[0][0], p, nrhs) * nhalf
+        return [torch.empty(n, dtype=torch.uint8, device="cuda") for _ in range(self.n)]
+
+    def canonical(self, nrhs: int = 1):
+        """One block-local canonical FP64 field per block."""
+        V = 2 * self.Vh
+        return [torch.zeros((nrhs, V, 4, 3), dtype=torch.complex128, device="cuda")
+                for _ in range(self.n)]
+
+    def close(self):
+        if self.handle is not None:
+            wl_dd_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

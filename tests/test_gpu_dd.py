@@ -1,0 +1,289 @@
+"""GPU parity of the domain-decomposed operator and solve (Sec. 4.4: pack the
+spin-projected faces, exchange them, interior sweep while they move, then the
+boundary) against the FP64 oracle on the undivided lattice.
+
+Cuts along t, t x z and y x z x t; a block extent of 2 along the cut (every
+site is a boundary site, and both faces of a block are one site apart); three
+blocks along t (distinct forward and backward neighbours); a twisted boundary
+phase on the cut direction.  Tolerances are those of the undivided operator
+(gpu_helpers.TOL); solves must reach an oracle true residual <= 1e-10.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_helpers import PRECS, TOL, rel
+from paper_1811_00893_gb300 import fields, wilson
+
+pytestmark = pytest.mark.gpu
+
+TW = np.exp(0.7j)
+CASES = [((4, 4, 4, 8), (1, 1, 1, 2), (1, 1, 1, -1)),       # t cut, 2 blocks
+         ((6, 4, 4, 4), (1, 1, 1, 2), (1, 1, 1, TW)),       # block extent 2 on the cut, twisted t phase
+         ((4, 4, 8, 8), (1, 1, 2, 2), (1, np.exp(0.2j), 1, -1)),  # t x z
+         ((4, 4, 4, 8), (1, 2, 2, 2), (1, 1, TW, -1)),      # 8 blocks, y x z x t, extent 2 in y, z
+         ((8, 4, 4, 12), (1, 1, 1, 3), (1, 1, 1, -1))]      # 3 blocks along t
+
+
+class DDCase:
+    def __init__(self, dims, grid, bc, kappa=0.124, seed=3, precs=("f64", "f32", "f16"), r12=False):
+        self.dims, self.grid, self.bc, self.kappa = tuple(dims), tuple(grid), bc, kappa
+        U = fields.gauge_field(dims, "haar", seed)
+        self.U = U.numpy()
+        self.U_dev = U.cuda().contiguous()
+        self.dd = wilson.Decomposition(dims, kappa, self.U_dev, grid, precs=precs, bc=bc, r12=r12)
+        self.V = int(np.prod(dims))
+
+    def to_blocks(self, psi_dev, parity, prec):
+        """Global canonical fields -> one internal half field per block."""
+        nrhs = psi_dev.shape[0]
+        loc = self.dd.canonical(nrhs)
+        wilson.wl_dd_scatter(self.dd.handle, loc, psi_dev, nrhs)
+        out = self.dd.field(prec, nrhs)
+        for k, (g, _) in enumerate(self.dd.blocks):
+            wilson.wl_field_to_internal(g, out[k], loc[k], parity, PRECS[prec], nrhs)
+        return out
+
+    def to_blocks_full(self, psi_dev, prec):
+        """Global canonical fields -> one [even | odd] internal field per block."""
+        nrhs = psi_dev.shape[0]
+        loc = self.dd.canonical(nrhs)
+        wilson.wl_dd_scatter(self.dd.handle, loc, psi_dev, nrhs)
+        g0 = self.dd.blocks[0][0]
+        fb = wilson.wl_field_bytes(g0, PRECS[prec], 1)
+        out = self.dd.field(prec, nrhs, nhalf=2)
+        for k, (g, _) in enumerate(self.dd.blocks):
+            for r in range(nrhs):
+                for p in (0, 1):
+                    seg = out[k][(2 * r + p) * fb:(2 * r + p + 1) * fb]
+                    wilson.wl_field_to_internal(g, seg, loc[k][r:r + 1], p, PRECS[prec], 1)
+        return out
+
+    def from_blocks(self, fields_, parity, prec, nrhs):
+        loc = self.dd.canonical(nrhs)
+        for k, (g, _) in enumerate(self.dd.blocks):
+            wilson.wl_field_to_canonical(g, loc[k], fields_[k], parity, PRECS[prec], nrhs)
+        out = torch.zeros((nrhs, self.V, 4, 3), dtype=torch.complex128, device="cuda")
+        wilson.wl_dd_gather(self.dd.handle, out, loc, nrhs)
+        return out
+
+    def from_blocks_full(self, fields_, prec, nrhs):
+        g0 = self.dd.blocks[0][0]
+        fb = wilson.wl_field_bytes(g0, PRECS[prec], 1)
+        loc = self.dd.canonical(nrhs)
+        for k, (g, _) in enumerate(self.dd.blocks):
+            for r in range(nrhs):
+                for p in (0, 1):
+                    seg = fields_[k][(2 * r + p) * fb:(2 * r + p + 1) * fb]
+                    wilson.wl_field_to_canonical(g, loc[k][r:r + 1], seg, p, PRECS[prec], 1)
+        out = torch.zeros((nrhs, self.V, 4, 3), dtype=torch.complex128, device="cuda")
+        wilson.wl_dd_gather(self.dd.handle, out, loc, nrhs)
+        return out
+
+    def half(self, canon, parity, r=0):
+        e, o = oracle.split(canon[r].cpu().numpy(), self.dims)
+        return e if parity == 0 else o
+
+    def close(self):
+        self.dd.close()
+
+
+@pytest.fixture(scope="module", params=CASES,
+                ids=lambda c: "x".join(map(str, c[0])) + "-g" + "".join(map(str, c[1])))
+def ddc(request):
+    dims, grid, bc = request.param
+    c = DDCase(dims, grid, bc)
+    yield c
+    c.close()
+
+
+def test_scatter_gather_round_trip(ddc):
+    psi = fields.gaussian_fermion(ddc.dims, 2, 5).cuda()
+    loc = ddc.dd.canonical(2)
+    wilson.wl_dd_scatter(ddc.dd.handle, loc, psi, 2)
+    back = torch.zeros_like(psi)
+    wilson.wl_dd_gather(ddc.dd.handle, back, loc, 2)
+    torch.cuda.synchronize()
+    assert torch.equal(back, psi)
+    # block 0 holds the sites of the first block of the grid
+    L = ddc.dd.local_dims
+    want = psi[0].reshape(ddc.dims[::-1] + (4, 3))[:L[3], :L[2], :L[1], :L[0]].reshape(-1, 4, 3)
+    assert torch.equal(loc[0][0], want)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df64"])
+@pytest.mark.parametrize("dagger", [0, 1])
+def test_dslash_dd_matches_oracle(ddc, prec, dagger):
+    nrhs = 2
+    psi = fields.gaussian_fermion(ddc.dims, nrhs, 21).cuda()
+    for out_parity in (0, 1):
+        inp = ddc.to_blocks(psi, 1 - out_parity, prec)
+        out = ddc.dd.field(prec, nrhs)
+        wilson.wilson_dslash_dd(ddc.dd.handle, out, inp, out_parity, dagger, PRECS[prec], nrhs)
+        got = ddc.from_blocks(out, out_parity, prec, nrhs)
+        for r in range(nrhs):
+            want = oracle.hop_eo(ddc.U, ddc.half(psi, 1 - out_parity, r), ddc.dims, ddc.bc, out_parity,
+                                 dagger=bool(dagger))
+            err = rel(ddc.half(got, out_parity, r), want)
+            assert err <= TOL[prec], (prec, dagger, out_parity, r, err)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df64"])
+def test_dslash_dd_equals_undivided(ddc, prec):
+    """Every site is computed once with the operations of the undivided
+    kernel and the halo carries exactly the half spinor that kernel forms, so
+    the decomposed result is bit for bit the undivided one."""
+    nrhs = 1
+    psi = fields.gaussian_fermion(ddc.dims, nrhs, 23).cuda()
+    g = wilson.Gauge(ddc.dims, ddc.kappa, ddc.U_dev, precs=("f64", "f32", "f16"), bc=ddc.bc)
+    try:
+        inp = g.field(prec, nrhs)
+        wilson.wl_field_to_internal(g.handle, inp, psi, 1, PRECS[prec], nrhs)
+        out = g.field(prec, nrhs)
+        wilson.wilson_dslash(g.handle, out, inp, 0, 0, PRECS[prec], nrhs)
+        ref = torch.zeros((nrhs, ddc.V, 4, 3), dtype=torch.complex128, device="cuda")
+        wilson.wl_field_to_canonical(g.handle, ref, out, 0, PRECS[prec], nrhs)
+        dout = ddc.dd.field(prec, nrhs)
+        wilson.wilson_dslash_dd(ddc.dd.handle, dout, ddc.to_blocks(psi, 1, prec), 0, 0, PRECS[prec], nrhs)
+        got = ddc.from_blocks(dout, 0, prec, nrhs)
+        assert torch.equal(got, ref), rel(ddc.half(got, 0), ddc.half(ref, 0))
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df64"])
+@pytest.mark.parametrize("dagger", [0, 1])
+def test_mult_dd_matches_oracle(ddc, prec, dagger):
+    nrhs = 2
+    psi = fields.gaussian_fermion(ddc.dims, nrhs, 31).cuda()
+    # eo = 1: M_ee on even half fields
+    inp = ddc.to_blocks(psi, 0, prec)
+    out = ddc.dd.field(prec, nrhs)
+    wilson.wilson_mult_dd(ddc.dd.handle, out, inp, 1, dagger, PRECS[prec], nrhs)
+    got = ddc.from_blocks(out, 0, prec, nrhs)
+    for r in range(nrhs):
+        want = oracle.Mee(ddc.U, ddc.half(psi, 0, r), ddc.dims, ddc.bc, ddc.kappa, dagger=bool(dagger))
+        err = rel(ddc.half(got, 0, r), want)
+        assert err <= TOL[prec], ("Mee", prec, dagger, r, err)
+    # eo = 0: full D on [even | odd] fields
+    inp = ddc.to_blocks_full(psi, prec)
+    out = ddc.dd.field(prec, nrhs, nhalf=2)
+    wilson.wilson_mult_dd(ddc.dd.handle, out, inp, 0, dagger, PRECS[prec], nrhs)
+    got = ddc.from_blocks_full(out, prec, nrhs)
+    for r in range(nrhs):
+        want = oracle.D_full(ddc.U, psi[r].cpu().numpy(), ddc.dims, ddc.bc, ddc.kappa, dagger=bool(dagger))
+        err = rel(got[r].cpu().numpy(), want)
+        assert err <= TOL[prec], ("D", prec, dagger, r, err)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_cdot_dd_is_the_global_sum(ddc, prec):
+    nrhs = 3
+    a = fields.gaussian_fermion(ddc.dims, nrhs, 41).cuda()
+    b = fields.gaussian_fermion(ddc.dims, nrhs, 42).cuda()
+    ia, ib = ddc.to_blocks(a, 0, prec), ddc.to_blocks(b, 0, prec)
+    out = torch.zeros(3 * nrhs, dtype=torch.float64, device="cuda")
+    wilson.wl_cdot_dd(ddc.dd.handle, out, ia, ib, PRECS[prec], nrhs)
+    # the oracle on the stored (rounded) fields gathered back
+    ga, gb = ddc.from_blocks(ia, 0, prec, nrhs), ddc.from_blocks(ib, 0, prec, nrhs)
+    o = out.view(nrhs, 3).cpu().numpy()
+    # per-site products in the storage type's arithmetic (2^-24 relative per
+    # term in FP32), sums in FP64
+    tol = {"f64": 1e-12, "f32": 1e-6}[prec]
+    for r in range(nrhs):
+        ea, eb = ddc.half(ga, 0, r), ddc.half(gb, 0, r)
+        c = oracle.cdot(ea, eb)
+        n2 = oracle.cdot(eb, eb).real
+        scale = np.sqrt(n2 * oracle.cdot(ea, ea).real)
+        assert abs(o[r, 0] - c.real) <= tol * scale
+        assert abs(o[r, 1] - c.imag) <= tol * scale
+        assert abs(o[r, 2] - n2) <= tol * n2
+
+
+@pytest.mark.parametrize("inner,delta", [("f32", 0.0), ("f64", 0.0), ("f16", 0.003)],
+                         ids=["f32-defect-correction", "f64", "f16-reliable"])
+def test_solve_dd_reaches_oracle_residual(ddc, inner, delta):
+    nrhs = 2
+    b = fields.gaussian_fermion(ddc.dims, nrhs, 51).cuda()
+    bl = ddc.dd.canonical(nrhs)
+    wilson.wl_dd_scatter(ddc.dd.handle, bl, b, nrhs)
+    xl = ddc.dd.canonical(nrhs)
+    prm = wilson.solve_params(tol=1e-10, eo=True, inner=PRECS[inner], delta=delta)
+    rc, info = wilson.wilson_solve_dd(ddc.dd.handle, xl, bl, nrhs, prm)
+    x = torch.zeros_like(b)
+    wilson.wl_dd_gather(ddc.dd.handle, x, xl, nrhs)
+    for r in range(nrhs):
+        tr = oracle.true_residual(ddc.U, b[r].cpu().numpy(), x[r].cpu().numpy(), ddc.dims, ddc.bc, ddc.kappa)
+        assert tr <= 1e-10, (inner, r, tr, info[r])
+        assert info[r]["status"] == 0 and info[r]["true_resid"] <= 1e-10
+
+
+def test_solve_dd_iterations_match_undivided():
+    """The decomposed FP64 solve takes the undivided solve's iterations (the
+    same Krylov sequence up to the summation order of the global sums)."""
+    c = DDCase((4, 4, 4, 8), (1, 1, 1, 2), (1, 1, 1, -1))
+    g = wilson.Gauge(c.dims, c.kappa, c.U_dev, precs=("f64",), bc=c.bc)
+    try:
+        b = fields.gaussian_fermion(c.dims, 1, 61).cuda()
+        prm = wilson.solve_params(tol=1e-10, eo=True, inner=wilson.WL_F64)
+        x = torch.zeros_like(b)
+        _, ref = wilson.wilson_solve(g.handle, x, b, 1, prm)
+        bl = c.dd.canonical(1)
+        wilson.wl_dd_scatter(c.dd.handle, bl, b, 1)
+        xl = c.dd.canonical(1)
+        _, got = wilson.wilson_solve_dd(c.dd.handle, xl, bl, 1, prm)
+        assert abs(got[0]["iters"] - ref[0]["iters"]) <= 1, (got, ref)
+    finally:
+        g.close()
+        c.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["copy", "direct"])
+def test_exchange_modes_agree(mode):
+    c = DDCase((4, 4, 8, 8), (1, 1, 2, 2), (1, 1, 1, -1))
+    try:
+        wilson.wl_dd_set_exchange(c.dd.handle, mode)
+        psi = fields.gaussian_fermion(c.dims, 1, 71).cuda()
+        inp = c.to_blocks(psi, 0, "f32")
+        out = c.dd.field("f32", 1)
+        wilson.wilson_mult_dd(c.dd.handle, out, inp, 1, 0, wilson.WL_F32, 1)
+        got = c.from_blocks(out, 0, "f32", 1)
+        want = oracle.Mee(c.U, c.half(psi, 0), c.dims, c.bc, c.kappa)
+        assert rel(c.half(got, 0), want) <= TOL["f32"]
+    finally:
+        c.close()
+
+
+def test_dd_compressed_links():
+    c = DDCase((6, 4, 4, 8), (1, 1, 2, 2), (1, 1, np.exp(0.4j), TW), precs=("f64", "f32", "f16"), r12=True)
+    try:
+        psi = fields.gaussian_fermion(c.dims, 1, 81).cuda()
+        for prec in ("f32", "f16"):
+            for dagger in (0, 1):
+                inp = c.to_blocks(psi, 1, prec)
+                out = c.dd.field(prec, 1)
+                wilson.wilson_dslash_dd(c.dd.handle, out, inp, 0, dagger, PRECS[prec], 1)
+                got = c.from_blocks(out, 0, prec, 1)
+                want = oracle.hop_eo(c.U, c.half(psi, 1), c.dims, c.bc, 0, dagger=bool(dagger))
+                assert rel(c.half(got, 0), want) <= TOL[prec], (prec, dagger)
+    finally:
+        c.close()
+
+
+def test_dd_errors():
+    U = fields.gauge_field((4, 4, 4, 8), "haar", 1).cuda()
+    lat = wilson.lattice((4, 4, 4, 8), 0.12)
+    for grid in [(2, 1, 1, 1), (1, 1, 1, 3), (1, 1, 1, 8), (1, 4, 4, 1)]:
+        with pytest.raises(wilson.WilsonError) as e:
+            wilson.wl_dd_create(lat, grid, U, wilson.prec_mask("f64"))
+        assert e.value.code == wilson.WL_ERR_ARG, grid
+    with wilson.Decomposition((4, 4, 4, 8), 0.12, U, (1, 1, 1, 2), precs=("f64",)) as dd:
+        g = dd.blocks[0][0]
+        f = dd.field("f64", 1)
+        with pytest.raises(wilson.WilsonError) as e:
+            wilson.wilson_dslash(g, f[0], f[1], 0, 0, wilson.WL_F64, 1)
+        assert e.value.code == wilson.WL_ERR_STATE
+        with pytest.raises(wilson.WilsonError) as e:
+            wilson.wilson_dslash_dd(dd.handle, f, f, 0, 0, wilson.WL_F32, 1)
+        assert e.value.code == wilson.WL_ERR_STATE  # no FP32 links
