@@ -288,14 +288,74 @@ int wilson_solve_batch(int nlat, const wl_gauge* gs, double* const* x, const dou
 typedef struct wl_dd_s* wl_dd;
 
 /* Create a decomposition of the lattice `lat` into grid[0..3] blocks (at most
- * 16), its links from the canonical FP64 gauge field U of the whole lattice
- * (device memory, read during the call).  prec_mask as for wl_gauge_create. */
+ * 16), all held by this process, its links from the canonical FP64 gauge
+ * field U of the whole lattice (device memory, read during the call).
+ * prec_mask as for wl_gauge_create. */
 int wl_dd_create(wl_dd* dd, const wl_lattice* lat, const int grid[4], const double* U, int prec_mask,
                  void* stream);
+
+/* One face message of a halo exchange (the "communication" step of Sec. 4.4):
+ * a packed face that one block sends to a neighbouring block, seen from one
+ * end.  Faces are the spin-projected half spinors of a block's x_mu = 0
+ * (side 0, sent to the backward neighbour) or x_mu = L_mu - 1 (side 1, sent
+ * to the forward neighbour) sites, 6 complex per face site in the
+ * arithmetic precision (FP64 / df64: 96 B, FP32 / FP16: 48 B per site),
+ * all right-hand sides back to back.  Layout of one right-hand side's face
+ * in FP64: 6 planes of one complex double per face site, plane 3 s + c
+ * holding spin row s (0 or 1) and colour c of (1 - gamma_mu) psi (side 0) or
+ * (1 + gamma_mu) psi (side 1) at that site (the dagger flips the signs); the
+ * two rows determine the other two.  Face sites are ordered by their half
+ * index with the mu coordinate dropped (x / 2 fastest, then the remaining
+ * directions in the order y, z, t). */
+typedef struct {
+    int send;       /* 1: send `bytes` at `buf` to block `peer`; 0: receive them from `peer` into `buf` */
+    int block;      /* the block of this process the message belongs to */
+    int peer;       /* the block at the other end */
+    int tag;        /* equal at both ends: 12 * (receiving block) + segment, segment =
+                       6 * launch parity + 2 * (mu - 1) + side */
+    size_t offset;  /* byte offset of the face in the block's send (send = 1) or halo region */
+    size_t bytes;
+    void* buf;      /* device address (NULL from wl_dd_plan) */
+} wl_dd_msg;
+
+/* How faces and global sums reach blocks held by other processes.  Both
+ * callbacks return 0 or a negative code (which the calling entry point
+ * returns as WL_ERR_CUDA); `stream` is the cudaStream_t whose earlier work
+ * produced the data, and work issued on it after the call must see the
+ * result (e.g. NCCL calls on that stream, or a synchronisation of it before
+ * host-side transfers that complete before returning).
+ *   exchange   perform every message of msgs (sends and receives);
+ *   allreduce  sum n doubles at buf (device) over all processes, in place;
+ *   all        nonzero: route faces between blocks of this process through
+ *              exchange too (otherwise they are device copies). */
+typedef struct {
+    void* ctx;
+    int (*exchange)(void* ctx, int nmsg, const wl_dd_msg* msgs, void* stream);
+    int (*allreduce)(void* ctx, double* buf, int n, void* stream);
+    int all;
+} wl_dd_transport;
+
+/* A decomposition of which this process holds blocks first .. first+count-1
+ * (at most 16); faces of other blocks and the global sums go through `tr`
+ * (required when count is below the number of blocks, optional otherwise;
+ * copied, and used until wl_dd_destroy).  U is the whole lattice's canonical
+ * gauge field on this device (its held blocks and their faces are read). */
+int wl_dd_create_part(wl_dd* dd, const wl_lattice* lat, const int grid[4], int first, int count,
+                      const double* U, int prec_mask, const wl_dd_transport* tr, void* stream);
+
+/* The face messages of block `block` of a decomposition of the lattice dims
+ * into grid blocks, for one hopping application of precision prec, nrhs
+ * right-hand sides and nparity (1 or 2) output parities: every message,
+ * local or not, with buf = NULL.  Host code only (no GPU needed).  Returns
+ * the number of messages (at most 24), or a negative code; writes at most
+ * max_msgs entries. */
+int wl_dd_plan(const int dims[4], const int grid[4], int block, wl_prec prec, int nrhs, int nparity,
+               wl_dd_msg* msgs, int max_msgs);
 int wl_dd_destroy(wl_dd dd);
-/* Number of blocks (0 for NULL). */
+/* Number of blocks this process holds (0 for NULL). */
 int wl_dd_blocks(wl_dd dd);
-/* Gauge object and grid coordinates of block k (either output may be NULL). */
+/* Gauge object and grid coordinates of the k-th block held here (either
+ * output may be NULL).  Arrays of block fields below are in this order. */
 int wl_dd_block(wl_dd dd, int k, wl_gauge* g, int coord[4]);
 /* Exchange of the packed faces: 0 = the pack kernel writes the block's own
  * send buffer and cudaMemcpyAsync moves each face to the neighbour's halo on
@@ -305,8 +365,9 @@ int wl_dd_block(wl_dd dd, int k, wl_gauge* g, int coord[4]);
 int wl_dd_set_exchange(wl_dd dd, int mode);
 
 /* Copy nrhs canonical FP64 fields of the whole lattice (`global`, device,
- * nrhs*V*12 complex) to block-local canonical fields (local[k], device,
- * nrhs*V_block*12 complex), and back.  Asynchronous. */
+ * nrhs*V*12 complex) to block-local canonical fields of the held blocks
+ * (local[k], device, nrhs*V_block*12 complex), and back (gather writes the
+ * held blocks' sites only).  Asynchronous. */
 int wl_dd_scatter(wl_dd dd, double* const* local, const double* global, int nrhs, void* stream);
 int wl_dd_gather(wl_dd dd, double* global, const double* const* local, int nrhs, void* stream);
 

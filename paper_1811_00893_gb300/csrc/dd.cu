@@ -60,31 +60,85 @@ struct DDFinish {
     int out_stride;
     const int* active;  // right-hand-side flags (every block holds the same)
     int active_stride;
+    // mode 0: write the total to every out; 1: write this process's total to
+    // stage (summed over the processes next); 2: copy stage to every out
+    int mode;
+    double* stage;
 };
 
-// One block per right-hand side: the total over the blocks, in block order
-// (the allreduce), written for every block.
+// One block per right-hand side: the total over the held blocks, in block
+// order (the allreduce when every block is held here), written for every
+// block or staged for the sum over the processes.
 __global__ void __launch_bounds__(256) dd_finish_kernel(const DDFinish F)
 {
     const int rhs = blockIdx.x;
     if (F.active && !F.active[(long long)rhs * F.active_stride]) return;
     __shared__ double sh[3 * 32];
     double tot[3] = {0.0, 0.0, 0.0};
-    for (int d = 0; d < F.ndom; ++d) {
-        double v[3];
-        if (F.nblocks > 0) {
-            sum_partials<3>(F.partial + d * F.dom_stride + (long long)rhs * F.max_blocks * 3, F.nblocks, v);
-            block_sum<3>(v, sh);
-        } else {
-            for (int k = 0; k < 3; ++k) v[k] = F.loc[d][3 * rhs + k];
+    if (F.mode == 2) {
+        for (int k = 0; k < 3; ++k) tot[k] = F.stage[3 * rhs + k];
+    } else {
+        for (int d = 0; d < F.ndom; ++d) {
+            double v[3];
+            if (F.nblocks > 0) {
+                sum_partials<3>(F.partial + d * F.dom_stride + (long long)rhs * F.max_blocks * 3, F.nblocks, v);
+                block_sum<3>(v, sh);
+            } else {
+                for (int k = 0; k < 3; ++k) v[k] = F.loc[d][3 * rhs + k];
+            }
+            if (threadIdx.x == 0)
+                for (int k = 0; k < 3; ++k) tot[k] += v[k];
         }
-        if (threadIdx.x == 0)
-            for (int k = 0; k < 3; ++k) tot[k] += v[k];
     }
-    if (threadIdx.x == 0)
-        for (int d = 0; d < F.ndom; ++d)
-            if (F.out[d])
-                for (int k = 0; k < 3; ++k) F.out[d][(long long)rhs * F.out_stride + k] = tot[k];
+    if (threadIdx.x != 0) return;
+    if (F.mode == 1) {
+        for (int k = 0; k < 3; ++k) F.stage[3 * rhs + k] = tot[k];
+        return;
+    }
+    for (int d = 0; d < F.ndom; ++d)
+        if (F.out[d])
+            for (int k = 0; k < 3; ++k) F.out[d][(long long)rhs * F.out_stride + k] = tot[k];
+}
+
+int dd_ensure_stage(wl_dd dd, int nrhs)
+{
+    if (nrhs <= dd->stage_rhs) return WL_OK;
+    WL_CUDA(cudaDeviceSynchronize());
+    if (dd->stage) cudaFree(dd->stage);
+    dd->stage = nullptr;
+    WL_CUDA(cudaMalloc((void**)&dd->stage, sizeof(double) * 3 * nrhs));
+    dd->stage_rhs = nrhs;
+    return WL_OK;
+}
+
+int dd_cross_sum(wl_dd dd, int nrhs, cudaStream_t s)
+{
+    if (!dd->has_tr) return WL_OK;
+    const int rc = dd->tr.allreduce(dd->tr.ctx, dd->stage, 3 * nrhs, (void*)s);
+    if (rc != 0) return set_error(WL_ERR_CUDA, "transport allreduce failed");
+    return WL_OK;
+}
+
+// Launch the finish kernel; with a transport, as local total -> sum over the
+// processes -> copy to every held block.
+static int dd_finish(wl_dd dd, DDFinish F, int nrhs, cudaStream_t s)
+{
+    if (!dd->has_tr) {
+        F.mode = 0;
+        dd_finish_kernel<<<nrhs, 256, 0, s>>>(F);
+        WL_CHECK_LAUNCH(0.0);
+        return WL_OK;
+    }
+    WL_TRY(dd_ensure_stage(dd, nrhs));
+    F.stage = dd->stage;
+    F.mode = 1;
+    dd_finish_kernel<<<nrhs, 256, 0, s>>>(F);
+    WL_CHECK_LAUNCH(0.0);
+    WL_TRY(dd_cross_sum(dd, nrhs, s));
+    F.mode = 2;
+    dd_finish_kernel<<<nrhs, 256, 0, s>>>(F);
+    WL_CHECK_LAUNCH(0.0);
+    return WL_OK;
 }
 
 int dd_allreduce(wl_dd dd, double* const* loc, double* const* out, int out_stride, int nrhs,
@@ -101,9 +155,7 @@ int dd_allreduce(wl_dd dd, double* const* loc, double* const* out, int out_strid
     F.out_stride = out_stride;
     F.active = active ? active[0] : nullptr;
     F.active_stride = active_stride;
-    dd_finish_kernel<<<nrhs, 256, 0, s>>>(F);
-    WL_CHECK_LAUNCH(0.0);
-    return WL_OK;
+    return dd_finish(dd, F, nrhs, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -156,6 +208,29 @@ static int ensure_loc(wl_dd dd, int nrhs)
 // one decomposed hopping application
 // ---------------------------------------------------------------------------
 
+void dd_segments(const Geom& g, int cut, int P, int nrhs, int np, long long (&hoff)[2][4][2], DDSeg (&seg)[12],
+                 int& nseg, long long& total, long long& bytes)
+{
+    const long long hsb = (long long)halo_site_bytes(P);
+    std::memset(hoff, 0, sizeof hoff);
+    nseg = 0;
+    total = 0;
+    bytes = 0;
+    for (int k = 0; k < np; ++k)
+        for (int mu = 1; mu < 4; ++mu)
+            if (cut & (1 << mu))
+                for (int side = 0; side < 2; ++side) {
+                    const long long fs = g.Vh / g.L[mu];
+                    hoff[k][mu][side] = bytes;
+                    bytes += fs * hsb * nrhs;
+                    seg[nseg++] = {k, mu, side, total, fs};
+                    total += fs;
+                }
+}
+
+// segment number of (launch parity, mu, side) in message tags
+static int seg_code(const DDSeg& S) { return 6 * S.pidx + 2 * (S.mu - 1) + S.side; }
+
 int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
 {
     const int P = h.prec;
@@ -169,24 +244,19 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
     const long long hsb = (long long)halo_site_bytes(P);
 
     // halo segments of (launch parity, mu, side), all right-hand sides each
-    long long hoff[2][4][2] = {};
-    long long off = 0;
+    long long hoff[2][4][2];
     DDSeg seg[12];
     int nseg = 0;
-    long long total = 0;
-    for (int k = 0; k < np; ++k)
-        for (int mu = 1; mu < 4; ++mu)
-            if (dd->cut & (1 << mu))
-                for (int side = 0; side < 2; ++side) {
-                    hoff[k][mu][side] = off;
-                    off += dd->fs[mu] * hsb * nrhs;
-                    seg[nseg++] = {k, mu, side, total, dd->fs[mu]};
-                    total += dd->fs[mu];
-                }
+    long long total = 0, off = 0;
+    dd_segments(g, dd->cut, P, nrhs, np, hoff, seg, nseg, total, off);
     WL_TRY(ensure_regions(dd, (size_t)off));
     const size_t sb = spinor_field_bytes(P, 1);
+    const bool route_all = dd->has_tr && dd->tr.all;
+    // a face goes straight into a held neighbour's halo in the direct mode
+    auto direct_to = [&](int to) { return dd->direct && !route_all && dd->local_of[to] >= 0; };
 
     // 1. pack, 2. exchange
+    bool exchanged = false;
     if (nseg) {
         DDPackArgs PA;
         std::memset(&PA, 0, sizeof PA);
@@ -202,24 +272,48 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
                 for (int side = 0; side < 2; ++side) {
                     // side 0 feeds the backward neighbour, side 1 the forward one
                     const int to = dd->peer[d][mu][side];
-                    PA.dst[d][mu][side] = dd->direct ? dd->recv[to] : dd->send[d];
+                    PA.dst[d][mu][side] = direct_to(to) ? dd->recv[dd->local_of[to]] : dd->send[d];
                 }
         }
         const dim3 grid((unsigned)((total + kDDBlock - 1) / kDDBlock), (unsigned)nrhs, (unsigned)dd->ndom);
         DDKernels<0>::pack(P, h.dagger != 0, PA, grid, s);
         WL_CHECK_LAUNCH((double)nrhs * dd->ndom * total * (sb + hsb));
-        if (!dd->direct) {
+        // faces that need moving: device copies between held blocks, messages
+        // through the transport for the rest
+        dd->msgs.clear();
+        bool copies = false;
+        for (int d = 0; d < dd->ndom; ++d)
+            for (int k = 0; k < nseg; ++k) {
+                const DDSeg& S = seg[k];
+                const long long o = hoff[S.pidx][S.mu][S.side];
+                const size_t bytes = (size_t)(S.count * hsb * nrhs);
+                const int to = dd->peer[d][S.mu][S.side], from = dd->peer[d][S.mu][1 - S.side];
+                if (dd->local_of[to] < 0 || route_all)
+                    dd->msgs.push_back({1, dd->gid[d], to, 12 * to + seg_code(S), (size_t)o, bytes, dd->send[d] + o});
+                else if (!direct_to(to))
+                    copies = true;
+                if (dd->local_of[from] < 0 || route_all)
+                    dd->msgs.push_back({0, dd->gid[d], from, 12 * dd->gid[d] + seg_code(S), (size_t)o, bytes,
+                                        dd->recv[d] + o});
+            }
+        if (copies || !dd->msgs.empty()) {
             WL_CUDA(cudaEventRecord(dd->ev_packed, s));
             WL_CUDA(cudaStreamWaitEvent(dd->comm, dd->ev_packed, 0));
-            for (int d = 0; d < dd->ndom; ++d)
-                for (int k = 0; k < nseg; ++k) {
-                    const DDSeg& S = seg[k];
-                    const int to = dd->peer[d][S.mu][S.side];
-                    const long long o = hoff[S.pidx][S.mu][S.side];
-                    WL_CUDA(cudaMemcpyAsync(dd->recv[to] + o, dd->send[d] + o, (size_t)(S.count * hsb * nrhs),
-                                            cudaMemcpyDeviceToDevice, dd->comm));
-                }
+            if (copies)
+                for (int d = 0; d < dd->ndom; ++d)
+                    for (int k = 0; k < nseg; ++k) {
+                        const DDSeg& S = seg[k];
+                        const int to = dd->peer[d][S.mu][S.side];
+                        if (dd->local_of[to] < 0 || route_all || direct_to(to)) continue;
+                        const long long o = hoff[S.pidx][S.mu][S.side];
+                        WL_CUDA(cudaMemcpyAsync(dd->recv[dd->local_of[to]] + o, dd->send[d] + o,
+                                                (size_t)(S.count * hsb * nrhs), cudaMemcpyDeviceToDevice, dd->comm));
+                    }
+            if (!dd->msgs.empty() &&
+                dd->tr.exchange(dd->tr.ctx, (int)dd->msgs.size(), dd->msgs.data(), (void*)dd->comm) != 0)
+                return set_error(WL_ERR_CUDA, "transport exchange failed");
             WL_CUDA(cudaEventRecord(dd->ev_exchanged, dd->comm));
+            exchanged = true;
         }
     }
 
@@ -284,7 +378,7 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
         return WL_OK;
     };
     WL_TRY(run(false));
-    if (nseg && !dd->direct) WL_CUDA(cudaStreamWaitEvent(s, dd->ev_exchanged, 0));
+    if (exchanged) WL_CUDA(cudaStreamWaitEvent(s, dd->ev_exchanged, 0));
     WL_TRY(run(true));
 
     // 5. the fused reductions, summed over the blocks
@@ -300,8 +394,7 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
         F.out_stride = h.dot_stride;
         F.active = h.active[0];
         F.active_stride = h.active_stride;
-        dd_finish_kernel<<<nrhs, 256, 0, s>>>(F);
-        WL_CHECK_LAUNCH(0.0);
+        WL_TRY(dd_finish(dd, F, nrhs, s));
     }
     return WL_OK;
 }
@@ -328,6 +421,7 @@ extern "C" int wl_dd_destroy(wl_dd dd)
     if (dd->bsites) cudaFree(dd->bsites);
     if (dd->partial) cudaFree(dd->partial);
     if (dd->loc) cudaFree(dd->loc);
+    if (dd->stage) cudaFree(dd->stage);
     if (dd->ev_packed) cudaEventDestroy(dd->ev_packed);
     if (dd->ev_exchanged) cudaEventDestroy(dd->ev_exchanged);
     if (dd->comm) cudaStreamDestroy(dd->comm);
@@ -335,33 +429,68 @@ extern "C" int wl_dd_destroy(wl_dd dd)
     return WL_OK;
 }
 
-extern "C" int wl_dd_create(wl_dd* out, const wl_lattice* lat, const int* grid, const double* U, int prec_mask,
-                            void* stream)
+// Block extents of a decomposition (WL_ERR_ARG when the grid does not fit).
+static int dd_local_dims(const int* dims, const int* grid, int* loc, int* nblk)
+{
+    if (!grid) return set_error(WL_ERR_ARG, "NULL block grid");
+    if (grid[0] != 1) return set_error(WL_ERR_ARG, "the x direction is never cut: grid[0] must be 1");
+    long long n = 1;
+    loc[0] = dims[0];
+    for (int mu = 1; mu < 4; ++mu) {
+        if (grid[mu] < 1) return set_error(WL_ERR_ARG, "grid entries must be >= 1");
+        if (dims[mu] % grid[mu]) return set_error(WL_ERR_ARG, "grid must divide the lattice extents");
+        loc[mu] = dims[mu] / grid[mu];
+        if (loc[mu] < 2 || loc[mu] % 2) return set_error(WL_ERR_ARG, "block extents must be even and >= 2");
+        n *= grid[mu];
+    }
+    if (n > (1 << 20)) return set_error(WL_ERR_ARG, "too many blocks");
+    *nblk = (int)n;
+    return WL_OK;
+}
+
+// Grid coordinates of block b and of its neighbours.
+static void block_coords(const int* grid, int b, int (&c)[4])
+{
+    c[0] = 0;
+    c[1] = b % grid[1];
+    c[2] = (b / grid[1]) % grid[2];
+    c[3] = b / (grid[1] * grid[2]);
+}
+static int block_peer(const int* grid, const int (&c)[4], int mu, int side)
+{
+    int cc[4] = {c[0], c[1], c[2], c[3]};
+    cc[mu] = (c[mu] + (side ? 1 : grid[mu] - 1)) % grid[mu];
+    return cc[1] + grid[1] * (cc[2] + grid[2] * cc[3]);
+}
+
+extern "C" int wl_dd_create_part(wl_dd* out, const wl_lattice* lat, const int* grid, int first, int count,
+                                 const double* U, int prec_mask, const wl_dd_transport* tr, void* stream)
 {
     WL_ENTRY();
     if (!out) return set_error(WL_ERR_ARG, "NULL output handle");
     *out = nullptr;
     WL_TRY(validate_lattice(lat));
-    if (!grid) return set_error(WL_ERR_ARG, "NULL block grid");
-    if (grid[0] != 1) return set_error(WL_ERR_ARG, "the x direction is never cut: grid[0] must be 1");
-    int ndom = 1;
     wl_lattice loc = *lat;
-    for (int mu = 1; mu < 4; ++mu) {
-        if (grid[mu] < 1) return set_error(WL_ERR_ARG, "grid entries must be >= 1");
-        if (lat->dims[mu] % grid[mu]) return set_error(WL_ERR_ARG, "grid must divide the lattice extents");
-        loc.dims[mu] = lat->dims[mu] / grid[mu];
-        if (loc.dims[mu] < 2 || loc.dims[mu] % 2)
-            return set_error(WL_ERR_ARG, "block extents must be even and >= 2");
-        ndom *= grid[mu];
-    }
-    if (ndom > kMaxDomains) return set_error(WL_ERR_ARG, "at most 16 blocks per decomposition");
+    int nblk = 0;
+    WL_TRY(dd_local_dims(lat->dims, grid, loc.dims, &nblk));
+    if (first < 0 || count < 1 || first + count > nblk)
+        return set_error(WL_ERR_ARG, "held blocks must lie in 0 .. (number of blocks) - 1");
+    if (count > kMaxDomains) return set_error(WL_ERR_ARG, "at most 16 blocks per process");
+    if (count < nblk && !tr) return set_error(WL_ERR_ARG, "blocks held elsewhere need a transport");
+    if (tr && (!tr->exchange || !tr->allreduce)) return set_error(WL_ERR_ARG, "transport without callbacks");
     cudaStream_t s = (cudaStream_t)stream;
     auto dd = new wl_dd_s();
     dd->global = *lat;
     dd->gglob = make_geom(lat->dims);
     dd->gloc = make_geom(loc.dims);
     for (int mu = 0; mu < 4; ++mu) dd->grid[mu] = grid[mu];
-    dd->ndom = ndom;
+    dd->nblk = nblk;
+    dd->ndom = count;
+    dd->local_of.assign(nblk, -1);
+    if (tr) {
+        dd->tr = *tr;
+        dd->has_tr = true;
+    }
     for (int mu = 1; mu < 4; ++mu)
         if (grid[mu] > 1) {
             dd->cut |= 1 << mu;
@@ -370,19 +499,18 @@ extern "C" int wl_dd_create(wl_dd* out, const wl_lattice* lat, const int* grid, 
     int rc = WL_OK;
     do {
         if (cudaGetDevice(&dd->device) != cudaSuccess) { rc = set_error(WL_ERR_CUDA, "cudaGetDevice"); break; }
-        for (int d = 0; d < ndom && rc == WL_OK; ++d) {
-            int c[4] = {0, d % grid[1], (d / grid[1]) % grid[2], d / (grid[1] * grid[2])};
+        for (int d = 0; d < count && rc == WL_OK; ++d) {
+            const int b = first + d;
+            dd->gid[d] = b;
+            dd->local_of[b] = d;
+            int c[4];
+            block_coords(grid, b, c);
             int org[4];
             for (int mu = 0; mu < 4; ++mu) {
                 dd->coord[d][mu] = c[mu];
                 org[mu] = c[mu] * loc.dims[mu];
+                for (int side = 0; side < 2; ++side) dd->peer[d][mu][side] = block_peer(grid, c, mu, side);
             }
-            for (int mu = 0; mu < 4; ++mu)
-                for (int side = 0; side < 2; ++side) {
-                    int cc[4] = {c[0], c[1], c[2], c[3]};
-                    cc[mu] = (c[mu] + (side ? 1 : grid[mu] - 1)) % grid[mu];
-                    dd->peer[d][mu][side] = cc[1] + grid[1] * (cc[2] + grid[2] * cc[3]);
-                }
             unsigned edge = 0;
             for (int mu = 0; mu < 4; ++mu) {
                 if (c[mu] == grid[mu] - 1) edge |= 1u << (2 * mu);  // forward face is the lattice's
@@ -399,10 +527,10 @@ extern "C" int wl_dd_create(wl_dd* out, const wl_lattice* lat, const int* grid, 
         for (long long i = 0; i < g.Vh; ++i) {
             const long long row = i / g.Lxh;
             const int c[4] = {0, (int)(row % g.L[1]), (int)((row / g.L[1]) % g.L[2]), (int)(row / ((long long)g.L[1] * g.L[2]))};
-            bool b = false;
+            bool bnd = false;
             for (int mu = 1; mu < 4; ++mu)
-                if ((dd->cut >> mu) & 1) b |= c[mu] == 0 || c[mu] == g.L[mu] - 1;
-            (b ? bs : is).push_back((int)i);
+                if ((dd->cut >> mu) & 1) bnd |= c[mu] == 0 || c[mu] == g.L[mu] - 1;
+            (bnd ? bs : is).push_back((int)i);
         }
         dd->nint = (long long)is.size();
         dd->nbnd = (long long)bs.size();
@@ -435,12 +563,64 @@ extern "C" int wl_dd_create(wl_dd* out, const wl_lattice* lat, const int* grid, 
     return WL_OK;
 }
 
+extern "C" int wl_dd_create(wl_dd* out, const wl_lattice* lat, const int* grid, const double* U, int prec_mask,
+                            void* stream)
+{
+    WL_ENTRY();
+    if (!out) return set_error(WL_ERR_ARG, "NULL output handle");
+    *out = nullptr;
+    WL_TRY(validate_lattice(lat));
+    int loc[4], nblk = 0;
+    WL_TRY(dd_local_dims(lat->dims, grid, loc, &nblk));
+    if (nblk > kMaxDomains) return set_error(WL_ERR_ARG, "at most 16 blocks per decomposition");
+    return wl_dd_create_part(out, lat, grid, 0, nblk, U, prec_mask, nullptr, stream);
+}
+
+extern "C" int wl_dd_plan(const int* dims, const int* grid, int block, wl_prec prec, int nrhs, int nparity,
+                          wl_dd_msg* msgs, int max_msgs)
+{
+    if (!dims) return set_error(WL_ERR_ARG, "NULL extents");
+    int loc[4], nblk = 0;
+    for (int mu = 0; mu < 4; ++mu)
+        if (dims[mu] < 2 || dims[mu] % 2) return set_error(WL_ERR_ARG, "lattice extents must be even and >= 2");
+    WL_TRY(dd_local_dims(dims, grid, loc, &nblk));
+    if (block < 0 || block >= nblk) return set_error(WL_ERR_ARG, "block index out of range");
+    if (prec < WL_F64 || prec > WL_DF64) return set_error(WL_ERR_ARG, "unknown precision");
+    if (nrhs < 1 || (nparity != 1 && nparity != 2)) return set_error(WL_ERR_ARG, "nrhs >= 1, nparity 1 or 2");
+    if (max_msgs > 0 && !msgs) return set_error(WL_ERR_ARG, "NULL message array");
+    int cut = 0;
+    for (int mu = 1; mu < 4; ++mu)
+        if (grid[mu] > 1) cut |= 1 << mu;
+    long long hoff[2][4][2];
+    DDSeg seg[12];
+    int nseg = 0;
+    long long total = 0, bytes = 0;
+    dd_segments(make_geom(loc), cut, prec, nrhs, nparity, hoff, seg, nseg, total, bytes);
+    const long long hsb = (long long)halo_site_bytes(prec);
+    int c[4];
+    block_coords(grid, block, c);
+    int n = 0;
+    for (int k = 0; k < nseg; ++k) {
+        const DDSeg& S = seg[k];
+        const size_t o = (size_t)hoff[S.pidx][S.mu][S.side];
+        const size_t b = (size_t)(S.count * hsb * nrhs);
+        const int to = block_peer(grid, c, S.mu, S.side), from = block_peer(grid, c, S.mu, 1 - S.side);
+        const wl_dd_msg m[2] = {{1, block, to, 12 * to + seg_code(S), o, b, nullptr},
+                                {0, block, from, 12 * block + seg_code(S), o, b, nullptr}};
+        for (const wl_dd_msg& q : m) {
+            if (n < max_msgs) msgs[n] = q;
+            ++n;
+        }
+    }
+    return n;
+}
+
 extern "C" int wl_dd_blocks(wl_dd dd) { return dd ? dd->ndom : 0; }
 
 extern "C" int wl_dd_block(wl_dd dd, int k, wl_gauge* g, int* coord)
 {
     if (!dd) return set_error(WL_ERR_ARG, "NULL decomposition");
-    if (k < 0 || k >= dd->ndom) return set_error(WL_ERR_ARG, "block index out of range");
+    if (k < 0 || k >= dd->ndom) return set_error(WL_ERR_ARG, "held-block index out of range");
     if (g) *g = dd->dom[k];
     if (coord)
         for (int mu = 0; mu < 4; ++mu) coord[mu] = dd->coord[k][mu];

@@ -22,6 +22,8 @@
 // allreduce).
 #pragma once
 
+#include <vector>
+
 #include "hop.cuh"
 #include "solver.cuh"
 
@@ -323,19 +325,24 @@ struct DDSolveWork;  // dd_solve.cu
 
 }  // namespace wl
 
-// A lattice cut into blocks, all held by this process on one GPU.  The
-// blocks are numbered lexicographically over the grid, y fastest.
+// A lattice cut into blocks; this process holds blocks gid[0..ndom) on one
+// GPU, the others (if any) are reached through the transport.  Blocks are
+// numbered lexicographically over the grid, y fastest.  Arrays indexed by d
+// are per held block; peer[] holds global block numbers.
 struct wl_dd_s {
     wl_lattice global;
     wl::Geom gglob;
     wl::Geom gloc;  // one block
     int grid[4];
-    int ndom = 0;
-    int cut = 0;  // bit mu: direction mu cut
+    int nblk = 0;  // blocks of the whole decomposition
+    int ndom = 0;  // blocks held here
+    int cut = 0;   // bit mu: direction mu cut
     int device = 0;
+    int gid[wl::kMaxDomains] = {};
+    std::vector<int> local_of;  // global block -> held index, -1 when held elsewhere
     wl_gauge dom[wl::kMaxDomains] = {};
     int coord[wl::kMaxDomains][4] = {};
-    int peer[wl::kMaxDomains][4][2] = {};  // block index of the neighbour [mu][0: backward, 1: forward]
+    int peer[wl::kMaxDomains][4][2] = {};  // neighbour block [mu][0: backward, 1: forward]
     unsigned edge[wl::kMaxDomains] = {};
     long long fs[4] = {0, 0, 0, 0};
     // interior and boundary half indices (the same for every block)
@@ -343,21 +350,27 @@ struct wl_dd_s {
     int* bsites = nullptr;
     long long nint = 0, nbnd = 0;
     // halo regions: recv (faces received) and send (packed faces), per block,
-    // each holding [launch parity][mu][side] segments for halo_rhs right-hand
-    // sides of the widest halo precision
+    // each holding [launch parity][mu][side] segments (offsets from dd_segments)
     char* recv[wl::kMaxDomains] = {};
     char* send[wl::kMaxDomains] = {};
     size_t region_bytes = 0;  // capacity of each recv / send region
     // per-block local sums of the reductions (3 doubles per right-hand side)
     double* loc = nullptr;
     int loc_rhs = 0;
-    int direct = 0;  // 1: the pack writes straight into the neighbours' halos (no copy)
+    int direct = 0;  // 1: the pack writes straight into held neighbours' halos (no copy)
     cudaStream_t comm = nullptr;
     cudaEvent_t ev_packed = nullptr, ev_exchanged = nullptr;
     // reduction partials of all blocks and the per-block local sums
     double* partial = nullptr;
     long long part_dom_stride = 0;
     int part_max_blocks = 0, part_rhs = 0;
+    // transport to the blocks held elsewhere; stage holds the sums that cross
+    // processes (3 doubles per right-hand side)
+    bool has_tr = false;
+    wl_dd_transport tr = {};
+    double* stage = nullptr;
+    int stage_rhs = 0;
+    std::vector<wl_dd_msg> msgs;
     wl::DDSolveWork* sw = nullptr;  // solver workspace (dd_solve.cu)
 };
 
@@ -373,5 +386,15 @@ int dd_allreduce(wl_dd dd, double* const* loc, double* const* out, int out_strid
                  const int* const* active, int active_stride, cudaStream_t s);
 // Solver workspace release (dd_solve.cu).
 void dd_free_solver(wl_dd dd);
+// Halo segments of one hopping application (launch parities np, precision P,
+// nrhs): offsets hoff[k][mu][side] within a region, segment list and the
+// region size; identical on every block of the decomposition.
+void dd_segments(const Geom& g, int cut, int P, int nrhs, int np, long long (&hoff)[2][4][2], DDSeg (&seg)[12],
+                 int& nseg, long long& total, long long& bytes);
+// Make dd->stage hold 3 * nrhs doubles.
+int dd_ensure_stage(wl_dd dd, int nrhs);
+// Sum the 3 * nrhs doubles of dd->stage over the processes (no-op without a
+// transport).
+int dd_cross_sum(wl_dd dd, int nrhs, cudaStream_t s);
 
 }  // namespace wl

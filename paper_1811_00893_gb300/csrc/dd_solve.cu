@@ -159,21 +159,31 @@ __global__ void __launch_bounds__(kDDVec) dd_update_xr_kernel(const DDVecs V)
 }
 
 // The allreduce of the x/r update: the total over all blocks' partials, then
-// every block's copy of the scalars advances with it.
-__global__ void __launch_bounds__(256) dd_advance_kernel(const DDVecs V, int ndom)
+// every block's copy of the scalars advances with it.  mode 0: both here;
+// mode 1: this process's total to stage (summed over the processes next);
+// mode 2: advance with the total in stage.
+__global__ void __launch_bounds__(256) dd_advance_kernel(const DDVecs V, int ndom, int mode, double* stage)
 {
     const int rhs = blockIdx.x;
     if (!V.sc[0][rhs].active) return;
     __shared__ double sh[3 * 32];
     double tot[3] = {0.0, 0.0, 0.0};
-    for (int d = 0; d < ndom; ++d) {
-        double v[3];
-        sum_partials<3>(V.part + d * V.part_dom_stride + (long long)rhs * V.part_blocks * 3, V.part_blocks, v);
-        block_sum<3>(v, sh);
-        if (threadIdx.x == 0)
-            for (int k = 0; k < 3; ++k) tot[k] += v[k];
+    if (mode == 2) {
+        for (int k = 0; k < 3; ++k) tot[k] = stage[3 * rhs + k];
+    } else {
+        for (int d = 0; d < ndom; ++d) {
+            double v[3];
+            sum_partials<3>(V.part + d * V.part_dom_stride + (long long)rhs * V.part_blocks * 3, V.part_blocks, v);
+            block_sum<3>(v, sh);
+            if (threadIdx.x == 0)
+                for (int k = 0; k < 3; ++k) tot[k] += v[k];
+        }
     }
     if (threadIdx.x != 0) return;
+    if (mode == 1) {
+        for (int k = 0; k < 3; ++k) stage[3 * rhs + k] = tot[k];
+        return;
+    }
     for (int d = 0; d < ndom; ++d) {
         Scal& S = V.sc[d][rhs];
         const cx<double> al = safe_alpha(S), om = safe_omega(S);
@@ -435,7 +445,16 @@ static int dd_iteration(wl_dd dd, DDSolveWork* w, int nrhs, cudaStream_t s)
         WL_CHECK_LAUNCH((5.0 * w->vb + 2.0 * V.rsx) * nrhs * dd->ndom);
         return WL_OK;
     }));
-    dd_advance_kernel<<<nrhs, 256, 0, s>>>(V, dd->ndom);
+    if (!dd->has_tr) {
+        dd_advance_kernel<<<nrhs, 256, 0, s>>>(V, dd->ndom, 0, nullptr);
+        WL_CHECK_LAUNCH(0.0);
+        return WL_OK;
+    }
+    WL_TRY(dd_ensure_stage(dd, nrhs));
+    dd_advance_kernel<<<nrhs, 256, 0, s>>>(V, dd->ndom, 1, dd->stage);
+    WL_CHECK_LAUNCH(0.0);
+    WL_TRY(dd_cross_sum(dd, nrhs, s));
+    dd_advance_kernel<<<nrhs, 256, 0, s>>>(V, dd->ndom, 2, dd->stage);
     WL_CHECK_LAUNCH(0.0);
     return WL_OK;
 }

@@ -96,6 +96,9 @@ def load() -> ctypes.CDLL:
             "wilson_solve_batch": (I, [I, P, P, P, P, ctypes.POINTER(wl_solve_params),
                                        ctypes.POINTER(wl_solve_info), P]),
             "wl_dd_create": (I, [ctypes.POINTER(P), ctypes.POINTER(wl_lattice), ctypes.POINTER(I), P, I, P]),
+            "wl_dd_create_part": (I, [ctypes.POINTER(P), ctypes.POINTER(wl_lattice), ctypes.POINTER(I),
+                                      I, I, P, I, P, P]),
+            "wl_dd_plan": (I, [ctypes.POINTER(I), ctypes.POINTER(I), I, I, I, I, P, I]),
             "wl_dd_destroy": (I, [P]),
             "wl_dd_blocks": (I, [P]),
             "wl_dd_block": (I, [P, I, ctypes.POINTER(P), ctypes.POINTER(I)]),
@@ -127,7 +130,7 @@ def exported_symbols():
     return ["wl_gauge_create", "wl_gauge_destroy", "wl_half_volume", "wl_field_bytes",
             "wl_field_to_internal", "wl_field_to_canonical", "wilson_dslash", "wilson_mult",
             "wl_clover_set", "wl_clover_apply", "wl_cdot", "wl_cdot_noalloc", "wilson_solve",
-            "wilson_solve_batch", "wl_dd_create", "wl_dd_destroy", "wl_dd_blocks", "wl_dd_block",
+            "wilson_solve_batch", "wl_dd_create", "wl_dd_create_part", "wl_dd_plan", "wl_dd_destroy", "wl_dd_blocks", "wl_dd_block",
             "wl_dd_set_exchange", "wl_dd_scatter", "wl_dd_gather", "wilson_dslash_dd",
             "wilson_mult_dd", "wl_cdot_dd", "wilson_solve_dd", "wl_last_error",
             "wl_spinor16_format",
@@ -286,6 +289,17 @@ def wl_dd_create(lat: wl_lattice, grid, U: torch.Tensor, mask: int, stream=None)
     return dd
 
 
+def wl_dd_create_part(lat: wl_lattice, grid, first: int, count: int, U: torch.Tensor, mask: int,
+                      transport=None, stream=None) -> ctypes.c_void_p:
+    """transport: a dd_transport.wl_dd_transport (or None when every block is held)."""
+    dd = ctypes.c_void_p()
+    G = (ctypes.c_int * 4)(*[int(k) for k in grid])
+    tp = ctypes.cast(ctypes.byref(transport), ctypes.c_void_p) if transport is not None else None
+    _check(load().wl_dd_create_part(ctypes.byref(dd), ctypes.byref(lat), G, int(first), int(count),
+                                    _ptr(U), int(mask), tp, _stream(stream)))
+    return dd
+
+
 def wl_dd_destroy(dd) -> None:
     _check(load().wl_dd_destroy(dd))
 
@@ -413,13 +427,22 @@ class Decomposition:
     """Owns a wl_dd handle: the lattice `dims` cut into `grid` blocks."""
 
     def __init__(self, dims, kappa, U: torch.Tensor, grid, precs=("f64", "f32", "f16"),
-                 bc=(1, 1, 1, -1), stream=None, r12: bool = False):
+                 bc=(1, 1, 1, -1), stream=None, r12: bool = False, held=None, transport=None):
+        """held = (first, count): the blocks this process holds (default: all),
+        with `transport` (dd_transport.TorchTransport) for the others."""
         self.dims = tuple(int(d) for d in dims)
         self.grid = tuple(int(k) for k in grid)
         self.kappa = float(kappa)
         self.lat = lattice(dims, kappa, bc)
         mask = prec_mask(*precs) | (WL_LINKS_R12 if r12 else 0)
-        self.handle = wl_dd_create(self.lat, self.grid, U, mask, stream)
+        self.transport = transport
+        if held is None and transport is None:
+            self.handle = wl_dd_create(self.lat, self.grid, U, mask, stream)
+        else:
+            nblk = self.grid[1] * self.grid[2] * self.grid[3]
+            first, count = held if held is not None else (0, nblk)
+            self.handle = wl_dd_create_part(self.lat, self.grid, first, count, U, mask,
+                                            transport.as_c() if transport is not None else None, stream)
         self.n = wl_dd_blocks(self.handle)
         self.blocks = [wl_dd_block(self.handle, k) for k in range(self.n)]
         self.local_dims = tuple(self.dims[m] // self.grid[m] for m in range(4))

@@ -13,7 +13,9 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "wi
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w]+\s*\*?\s*(\w+)\s*\(", src, flags=re.M))
+    # a type, then whitespace or a '*', then the function name and '(' (a
+    # function-pointer member such as "int (*f)(...)" is not a declaration)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:\w+\s+)*\w+(?:\s+|\s*\*\s*)(\w+)\s*\(", src, flags=re.M))
                   - {"if", "while", "for", "return", "sizeof"})
 
 

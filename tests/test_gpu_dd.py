@@ -287,3 +287,167 @@ def test_dd_errors():
         with pytest.raises(wilson.WilsonError) as e:
             wilson.wilson_dslash_dd(dd.handle, f, f, 0, 0, wilson.WL_F32, 1)
         assert e.value.code == wilson.WL_ERR_STATE  # no FP32 links
+
+
+# ----------------------------------------------------------------------------
+# the transport path: faces and sums through wl_dd_transport callbacks
+# ----------------------------------------------------------------------------
+
+def _mee_blocks(c, psi, prec="f32"):
+    inp = c.to_blocks(psi, 0, prec)
+    out = c.dd.field(prec, psi.shape[0])
+    wilson.wilson_mult_dd(c.dd.handle, out, inp, 1, 0, PRECS[prec], psi.shape[0])
+    return c.from_blocks(out, 0, prec, psi.shape[0])
+
+
+def test_transport_callbacks_match_device_copies():
+    """Every face of a one-process decomposition routed through the Python
+    transport gives the built-in copies' results bit for bit."""
+    from paper_1811_00893_gb300 import dd_transport
+    dims, grid, bc = (4, 4, 8, 8), (1, 1, 2, 2), (1, 1, 1, -1)
+    ref = DDCase(dims, grid, bc)
+    tr = dd_transport.TorchTransport(rank_of=lambda b: 0, rank=0, route_all=True)
+    c = DDCase(dims, grid, bc)
+    c.dd.close()
+    c.dd = wilson.Decomposition(dims, c.kappa, c.U_dev, grid, bc=bc, transport=tr)
+    try:
+        psi = fields.gaussian_fermion(dims, 2, 91).cuda()
+        for prec in ("f64", "f32", "f16"):
+            assert torch.equal(_mee_blocks(c, psi, prec), _mee_blocks(ref, psi, prec)), prec
+        assert tr.calls["exchange"] >= 6
+        b = fields.gaussian_fermion(dims, 1, 92).cuda()
+        bl = c.dd.canonical(1)
+        wilson.wl_dd_scatter(c.dd.handle, bl, b, 1)
+        xl = c.dd.canonical(1)
+        rc, info = wilson.wilson_solve_dd(c.dd.handle, xl, bl, 1, wilson.solve_params(tol=1e-10, inner=wilson.WL_F32))
+        x = torch.zeros_like(b)
+        wilson.wl_dd_gather(c.dd.handle, x, xl, 1)
+        assert oracle.true_residual(c.U, b[0].cpu().numpy(), x[0].cpu().numpy(), dims, bc, c.kappa) <= 1e-10
+        assert tr.calls["allreduce"] > 0
+    finally:
+        c.close()
+        ref.close()
+
+
+class ThreadTransport:
+    """Two holders of blocks in one process, one per host thread, sharing one
+    GPU: faces and sums meet in a host-side mailbox.  Every transfer is
+    host-synchronised (the sender's stream is synchronised before its face is
+    posted, the receiver copies and synchronises before acknowledging), so no
+    kernel ever waits on another holder's work."""
+
+    def __init__(self, holders: int):
+        import threading
+        self.cv = threading.Condition()
+        self.box = {}
+        self.acks = {}
+        self.sums = {}
+        self.round = 0
+        self.holders = holders
+
+    def for_holder(self, rank, rank_of):
+        from paper_1811_00893_gb300 import dd_transport
+        outer = self
+
+        class Holder(dd_transport.TorchTransport):
+            def exchange(self, msgs):
+                self.calls["exchange"] += 1
+                torch.cuda.current_stream().synchronize()
+                with outer.cv:
+                    for m in msgs:
+                        if m["send"]:
+                            outer.box[m["tag"]] = m["buf"]
+                    outer.cv.notify_all()
+                for m in msgs:
+                    if not m["send"]:
+                        with outer.cv:
+                            outer.cv.wait_for(lambda: m["tag"] in outer.box, timeout=60)
+                            src = outer.box.pop(m["tag"])
+                        m["buf"].copy_(src)
+                torch.cuda.current_stream().synchronize()
+                with outer.cv:
+                    for m in msgs:
+                        if not m["send"]:
+                            outer.acks[m["tag"]] = True
+                    outer.cv.notify_all()
+                    for m in msgs:  # our faces have been read: the buffer may be reused
+                        if m["send"]:
+                            outer.cv.wait_for(lambda: m["tag"] in outer.acks, timeout=60)
+                            outer.acks.pop(m["tag"])
+
+            def allreduce(self, t):
+                self.calls["allreduce"] += 1
+                val = t.cpu()
+                with outer.cv:
+                    r = outer.round
+                    outer.sums.setdefault(r, []).append(val)
+                    if len(outer.sums[r]) == outer.holders:
+                        outer.round += 1
+                        outer.cv.notify_all()
+                    else:
+                        outer.cv.wait_for(lambda: outer.round > r, timeout=60)
+                    vals = outer.sums[r]
+                total = vals[0].clone()
+                for v in vals[1:]:
+                    total += v
+                t.copy_(total.to(t.device))
+                torch.cuda.current_stream().synchronize()
+
+        return Holder(rank_of=rank_of, rank=rank)
+
+
+def test_two_holders_reach_the_undivided_results():
+    """A t-cut lattice whose two blocks are held by two holders (threads), as
+    two processes would hold them: the decomposed M_ee and an FP32
+    defect-correction solve through the transport callbacks."""
+    import threading
+    dims, grid, bc, kappa = (4, 4, 4, 8), (1, 1, 1, 2), (1, 1, 1, -1), 0.124
+    U = fields.gauge_field(dims, "haar", 3)
+    Un, Ud = U.numpy(), U.cuda()
+    psi = fields.gaussian_fermion(dims, 1, 93).cuda()
+    ref = DDCase(dims, grid, bc)
+    want = _mee_blocks(ref, psi)
+    ref.close()
+    tt = ThreadTransport(2)
+    results, errors = {}, []
+
+    def holder(rank):
+        try:
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                tr = tt.for_holder(rank, rank_of=lambda b: b)
+                dd = wilson.Decomposition(dims, kappa, Ud, grid, bc=bc, held=(rank, 1), transport=tr)
+                loc = dd.canonical(1)
+                wilson.wl_dd_scatter(dd.handle, loc, psi, 1)
+                g = dd.blocks[0][0]
+                inp = dd.field("f32", 1)
+                wilson.wl_field_to_internal(g, inp[0], loc[0], 0, wilson.WL_F32, 1)
+                out = dd.field("f32", 1)
+                wilson.wilson_mult_dd(dd.handle, out, inp, 1, 0, wilson.WL_F32, 1)
+                back = dd.canonical(1)
+                wilson.wl_field_to_canonical(g, back[0], out[0], 0, wilson.WL_F32, 1)
+                mee = torch.zeros_like(psi)
+                wilson.wl_dd_gather(dd.handle, mee, back, 1)
+                xl = dd.canonical(1)
+                rc, info = wilson.wilson_solve_dd(dd.handle, xl, loc, 1,
+                                                  wilson.solve_params(tol=1e-10, inner=wilson.WL_F32))
+                x = torch.zeros_like(psi)
+                wilson.wl_dd_gather(dd.handle, x, xl, 1)
+                stream.synchronize()
+                results[rank] = (mee, x, info[0], tr.calls)
+                dd.close()
+        except Exception as e:  # reported by the main thread
+            errors.append(repr(e))
+
+    ths = [threading.Thread(target=holder, args=(r,)) for r in range(2)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join(timeout=600)
+    assert not errors, errors
+    mee = results[0][0] + results[1][0]  # each holder gathered its own block's sites
+    assert torch.equal(mee, want)
+    x = results[0][1] + results[1][1]
+    assert oracle.true_residual(Un, psi[0].cpu().numpy(), x[0].cpu().numpy(), dims, bc, kappa) <= 1e-10
+    assert results[0][2]["iters"] == results[1][2]["iters"]
+    assert results[0][3]["allreduce"] > 0 and results[0][3]["exchange"] > 0
