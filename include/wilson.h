@@ -271,12 +271,13 @@ int wilson_solve_batch(int nlat, const wl_gauge* gs, double* const* x, const dou
  * with block-local canonical fields).  The hopping term of a block reads the
  * neighbouring blocks' spinors through halo buffers: each application packs
  * the spin-projected half spinors of the cut faces (12 reals per face site),
- * moves them to the neighbours' halos (device copies on a second stream, or,
- * in the direct mode, written there by the pack kernel itself), computes the
- * interior sites while the faces move, then the boundary sites.  Global sums
- * are formed per block and added over the blocks in block order.  Results
- * equal those of the undivided lattice up to the summation order of the
- * global sums.
+ * moves them to the neighbours' halos (a copy kernel, or, in the direct mode,
+ * the pack kernel writes them there itself) and computes the boundary sites,
+ * all on a second stream while the interior sites are computed on `stream`.
+ * Global sums are formed per block and added over the blocks in block order.
+ * Every output site is computed with the undivided kernel's operations, so
+ * the hopping term is bit for bit that of the undivided lattice; sums differ
+ * by their summation order.
  *
  * All blocks live on the calling thread's current GPU.  The calls are
  * asynchronous on `stream` except wl_dd_create, wl_dd_destroy,
@@ -357,11 +358,12 @@ int wl_dd_blocks(wl_dd dd);
 /* Gauge object and grid coordinates of the k-th block held here (either
  * output may be NULL).  Arrays of block fields below are in this order. */
 int wl_dd_block(wl_dd dd, int k, wl_gauge* g, int coord[4]);
-/* Exchange of the packed faces: 0 = the pack kernel writes the block's own
- * send buffer and cudaMemcpyAsync moves each face to the neighbour's halo on
- * a second stream, overlapping the interior sweep (the default); 1 = the pack
- * kernel writes straight into the neighbours' halos.  Synchronises the
- * device. */
+/* Exchange of the packed faces between blocks of this process: 0 = the pack
+ * kernel writes each block's own send buffer and one copy kernel moves every
+ * face to the neighbour's halo (the default; the step a transport takes over
+ * for blocks held elsewhere); 1 = the pack kernel writes straight into the
+ * neighbours' halos.  Both run on a second stream, overlapping the interior
+ * sweep.  Synchronises the device. */
 int wl_dd_set_exchange(wl_dd dd, int mode);
 
 /* Copy nrhs canonical FP64 fields of the whole lattice (`global`, device,

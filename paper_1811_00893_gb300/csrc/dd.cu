@@ -48,6 +48,46 @@ __global__ void dd_copy_canonical_kernel(double* loc, double* glob, Geom gl, Geo
 }
 
 // ---------------------------------------------------------------------------
+// the exchange between blocks held here: one copy kernel over all faces
+// ---------------------------------------------------------------------------
+
+static constexpr int kCopySegs = 64;  // face copies per launch
+
+struct DDCopies {
+    const uint4* src[kCopySegs];
+    uint4* dst[kCopySegs];
+    long long n16[kCopySegs];  // 16-byte words of each copy
+    long long start[kCopySegs + 1];  // prefix sums of n16
+    int n;
+};
+
+// grid-stride over the concatenated copies (every face segment is a multiple
+// of 16 bytes: 48 or 96 bytes per face site)
+__global__ void __launch_bounds__(256) dd_copy_kernel(const DDCopies C)
+{
+    const long long total = C.start[C.n];
+    for (long long j = blockIdx.x * 256LL + threadIdx.x; j < total; j += (long long)gridDim.x * 256) {
+        int k = 0;
+        while (k + 1 < C.n && j >= C.start[k + 1]) ++k;
+        const long long o = j - C.start[k];
+        C.dst[k][o] = __ldcs(C.src[k] + o);
+    }
+}
+
+static int launch_copies(DDCopies& C, cudaStream_t s)
+{
+    if (C.n == 0) return WL_OK;
+    C.start[0] = 0;
+    for (int k = 0; k < C.n; ++k) C.start[k + 1] = C.start[k] + C.n16[k];
+    const long long total = C.start[C.n];
+    const unsigned grid = (unsigned)std::min<long long>((total + 255) / 256, 4 * 152);
+    dd_copy_kernel<<<grid, 256, 0, s>>>(C);
+    WL_CHECK_LAUNCH(32.0 * total);
+    C.n = 0;
+    return WL_OK;
+}
+
+// ---------------------------------------------------------------------------
 // sums over the blocks
 // ---------------------------------------------------------------------------
 
@@ -255,69 +295,10 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
     // a face goes straight into a held neighbour's halo in the direct mode
     auto direct_to = [&](int to) { return dd->direct && !route_all && dd->local_of[to] >= 0; };
 
-    // 1. pack, 2. exchange
-    bool exchanged = false;
-    if (nseg) {
-        DDPackArgs PA;
-        std::memset(&PA, 0, sizeof PA);
-        PA.g = g;
-        std::memcpy(PA.seg, seg, sizeof seg);
-        PA.nseg = nseg;
-        PA.total = total;
-        std::memcpy(PA.hoff, hoff, sizeof hoff);
-        PA.rs_in = h.rs_in;
-        for (int d = 0; d < dd->ndom; ++d) {
-            for (int k = 0; k < np; ++k) PA.in[d][k] = (const char*)h.in[d][k];
-            for (int mu = 1; mu < 4; ++mu)
-                for (int side = 0; side < 2; ++side) {
-                    // side 0 feeds the backward neighbour, side 1 the forward one
-                    const int to = dd->peer[d][mu][side];
-                    PA.dst[d][mu][side] = direct_to(to) ? dd->recv[dd->local_of[to]] : dd->send[d];
-                }
-        }
-        const dim3 grid((unsigned)((total + kDDBlock - 1) / kDDBlock), (unsigned)nrhs, (unsigned)dd->ndom);
-        DDKernels<0>::pack(P, h.dagger != 0, PA, grid, s);
-        WL_CHECK_LAUNCH((double)nrhs * dd->ndom * total * (sb + hsb));
-        // faces that need moving: device copies between held blocks, messages
-        // through the transport for the rest
-        dd->msgs.clear();
-        bool copies = false;
-        for (int d = 0; d < dd->ndom; ++d)
-            for (int k = 0; k < nseg; ++k) {
-                const DDSeg& S = seg[k];
-                const long long o = hoff[S.pidx][S.mu][S.side];
-                const size_t bytes = (size_t)(S.count * hsb * nrhs);
-                const int to = dd->peer[d][S.mu][S.side], from = dd->peer[d][S.mu][1 - S.side];
-                if (dd->local_of[to] < 0 || route_all)
-                    dd->msgs.push_back({1, dd->gid[d], to, 12 * to + seg_code(S), (size_t)o, bytes, dd->send[d] + o});
-                else if (!direct_to(to))
-                    copies = true;
-                if (dd->local_of[from] < 0 || route_all)
-                    dd->msgs.push_back({0, dd->gid[d], from, 12 * dd->gid[d] + seg_code(S), (size_t)o, bytes,
-                                        dd->recv[d] + o});
-            }
-        if (copies || !dd->msgs.empty()) {
-            WL_CUDA(cudaEventRecord(dd->ev_packed, s));
-            WL_CUDA(cudaStreamWaitEvent(dd->comm, dd->ev_packed, 0));
-            if (copies)
-                for (int d = 0; d < dd->ndom; ++d)
-                    for (int k = 0; k < nseg; ++k) {
-                        const DDSeg& S = seg[k];
-                        const int to = dd->peer[d][S.mu][S.side];
-                        if (dd->local_of[to] < 0 || route_all || direct_to(to)) continue;
-                        const long long o = hoff[S.pidx][S.mu][S.side];
-                        WL_CUDA(cudaMemcpyAsync(dd->recv[dd->local_of[to]] + o, dd->send[d] + o,
-                                                (size_t)(S.count * hsb * nrhs), cudaMemcpyDeviceToDevice, dd->comm));
-                    }
-            if (!dd->msgs.empty() &&
-                dd->tr.exchange(dd->tr.ctx, (int)dd->msgs.size(), dd->msgs.data(), (void*)dd->comm) != 0)
-                return set_error(WL_ERR_CUDA, "transport exchange failed");
-            WL_CUDA(cudaEventRecord(dd->ev_exchanged, dd->comm));
-            exchanged = true;
-        }
-    }
-
-    // 3. interior, 4. boundary
+    // Two streams: the interior sweep on `s`; pack -> exchange -> boundary on
+    // the side stream, at the same time (the interior needs no face, and the
+    // two sweeps write disjoint sites and reduction slots).  The side stream
+    // first waits for everything issued on `s` before this call.
     DDArgs A;
     std::memset(&A, 0, sizeof A);
     A.g = g;
@@ -353,6 +334,7 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
         D.active = h.active[d];
         D.edge = dd->edge[d];
     }
+    const bool t_only = dd->cut == (1 << 3);
     const int bi = (int)((dd->nint + kDDBlock - 1) / kDDBlock);
     const int bb = (int)((dd->nbnd + kDDBlock - 1) / kDDBlock);
     if (h.dot) {
@@ -364,22 +346,80 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
     const int extra = (h.x1[0][0] ? 1 : 0) + (h.x2[0][0] ? 1 : 0) + (h.w[0][0] ? 1 : 0);
     const double site_bytes = (double)(lf ? (P == WL_F32 ? 384 : 192) : link_field_bytes(P, 1)) +
                               (double)nrhs * (2 + extra) * sb;
-    auto run = [&](bool bnd) -> int {
-        const long long n = bnd ? dd->nbnd : dd->nint;
+    // part 0: interior (one contiguous range when only t is cut), part 1: boundary
+    auto run = [&](int part, DDArgs AA, cudaStream_t st_) -> int {
+        const long long n = part ? dd->nbnd : dd->nint;
         if (n == 0) return WL_OK;
-        A.sites = bnd ? dd->bsites : dd->isites;
-        A.nsites = n;
-        A.blocks_per_parity = bnd ? bb : bi;
-        A.block0 = bnd ? np * bi : 0;
-        const dim3 grid((unsigned)(A.blocks_per_parity * np), (unsigned)nrhs, (unsigned)dd->ndom);
-        if (lf) DDKernels<1>::hop(P, h.dagger != 0, h.dot, bnd, A, grid, s);
-        else DDKernels<0>::hop(P, h.dagger != 0, h.dot, bnd, A, grid, s);
+        AA.sites = part ? dd->bsites : (t_only ? nullptr : dd->isites);
+        AA.site0 = (!part && t_only) ? g.st : 0;
+        AA.nsites = n;
+        AA.blocks_per_parity = part ? bb : bi;
+        AA.block0 = part ? np * bi : 0;
+        const dim3 grid((unsigned)(AA.blocks_per_parity * np), (unsigned)nrhs, (unsigned)dd->ndom);
+        if (lf) DDKernels<1>::hop(P, h.dagger != 0, h.dot, part == 1, AA, grid, st_);
+        else DDKernels<0>::hop(P, h.dagger != 0, h.dot, part == 1, AA, grid, st_);
         WL_CHECK_LAUNCH((double)dd->ndom * np * n * site_bytes);
         return WL_OK;
     };
-    WL_TRY(run(false));
-    if (exchanged) WL_CUDA(cudaStreamWaitEvent(s, dd->ev_exchanged, 0));
-    WL_TRY(run(true));
+    if (!nseg) {  // nothing cut: every site is interior
+        WL_TRY(run(0, A, s));
+    } else {
+        WL_CUDA(cudaEventRecord(dd->ev_packed, s));
+        WL_CUDA(cudaStreamWaitEvent(dd->comm, dd->ev_packed, 0));
+        WL_TRY(run(0, A, s));
+        // 1. pack
+        DDPackArgs PA;
+        std::memset(&PA, 0, sizeof PA);
+        PA.g = g;
+        std::memcpy(PA.seg, seg, sizeof seg);
+        PA.nseg = nseg;
+        PA.total = total;
+        std::memcpy(PA.hoff, hoff, sizeof hoff);
+        PA.rs_in = h.rs_in;
+        for (int d = 0; d < dd->ndom; ++d) {
+            for (int k = 0; k < np; ++k) PA.in[d][k] = (const char*)h.in[d][k];
+            for (int mu = 1; mu < 4; ++mu)
+                for (int side = 0; side < 2; ++side) {
+                    // side 0 feeds the backward neighbour, side 1 the forward one
+                    const int to = dd->peer[d][mu][side];
+                    PA.dst[d][mu][side] = direct_to(to) ? dd->recv[dd->local_of[to]] : dd->send[d];
+                }
+        }
+        const dim3 grid((unsigned)((total + kDDBlock - 1) / kDDBlock), (unsigned)nrhs, (unsigned)dd->ndom);
+        DDKernels<0>::pack(P, h.dagger != 0, PA, grid, dd->comm);
+        WL_CHECK_LAUNCH((double)nrhs * dd->ndom * total * (sb + hsb));
+        // 2. exchange: device copies between held blocks, messages through the
+        // transport for the rest
+        dd->msgs.clear();
+        DDCopies C;
+        C.n = 0;
+        for (int d = 0; d < dd->ndom; ++d)
+            for (int k = 0; k < nseg; ++k) {
+                const DDSeg& S = seg[k];
+                const long long o = hoff[S.pidx][S.mu][S.side];
+                const size_t bytes = (size_t)(S.count * hsb * nrhs);
+                const int to = dd->peer[d][S.mu][S.side], from = dd->peer[d][S.mu][1 - S.side];
+                if (dd->local_of[to] < 0 || route_all) {
+                    dd->msgs.push_back({1, dd->gid[d], to, 12 * to + seg_code(S), (size_t)o, bytes, dd->send[d] + o});
+                } else if (!direct_to(to)) {
+                    C.src[C.n] = (const uint4*)(dd->send[d] + o);
+                    C.dst[C.n] = (uint4*)(dd->recv[dd->local_of[to]] + o);
+                    C.n16[C.n] = (long long)(bytes / 16);
+                    if (++C.n == kCopySegs) WL_TRY(launch_copies(C, dd->comm));
+                }
+                if (dd->local_of[from] < 0 || route_all)
+                    dd->msgs.push_back({0, dd->gid[d], from, 12 * dd->gid[d] + seg_code(S), (size_t)o, bytes,
+                                        dd->recv[d] + o});
+            }
+        WL_TRY(launch_copies(C, dd->comm));
+        if (!dd->msgs.empty() &&
+            dd->tr.exchange(dd->tr.ctx, (int)dd->msgs.size(), dd->msgs.data(), (void*)dd->comm) != 0)
+            return set_error(WL_ERR_CUDA, "transport exchange failed");
+        // 3. boundary on the side stream, then the main stream waits for it
+        WL_TRY(run(1, A, dd->comm));
+        WL_CUDA(cudaEventRecord(dd->ev_exchanged, dd->comm));
+        WL_CUDA(cudaStreamWaitEvent(s, dd->ev_exchanged, 0));
+    }
 
     // 5. the fused reductions, summed over the blocks
     if (h.dot) {

@@ -9,12 +9,14 @@
 //   pack      the spin-projected half spinors (12 reals, Eq. 1's (1 -+ gamma)
 //             acting on the neighbour) of the block's faces, per cut
 //             direction and side, for the neighbouring blocks;
-//   exchange  the packed faces travel to the neighbours' halo buffers (here
-//             device copies on a side stream: the paper's "communication =
-//             copy" mode of Sec. 5.2.3);
-//   interior  sites none of whose hops leave the block, while the exchange runs;
+//   exchange  the packed faces travel to the neighbours' halo buffers (a copy
+//             kernel between blocks of one process -- the paper's
+//             "communication = copy" mode of Sec. 5.2.3 -- or a transport);
+//   interior  sites none of whose hops leave the block, on the main stream;
 //   boundary  the remaining sites, with the hops that leave the block read from
 //             the halo.
+// Pack, exchange and boundary run on a side stream while the interior runs,
+// so the exchange and the boundary sweep's latency hide behind the bulk.
 //
 // Every output site is computed once, by one thread, with the same
 // operations as the undivided kernel.  Global sums (the BiCGStab dots) are
@@ -165,7 +167,8 @@ struct DDArgs {
     // (fs[mu] face sites of halo_planes(P) planes each)
     long long hoff[2][4][2];
     int active_stride;
-    const int* sites;      // the launch's sites: interior or boundary half indices
+    const int* sites;      // the launch's sites: interior or boundary half indices, or
+    long long site0;       // (sites == nullptr) the contiguous range site0 .. site0 + nsites - 1
     long long nsites;
     int blocks_per_parity;
     int parity0;
@@ -206,10 +209,13 @@ __device__ __forceinline__ void dd_hop_one(cx<typename Prec<P>::real> (&acc)[12]
                                            bool remote)
 {
     using T = typename Prec<P>::real;
-    cx<T> h0[3], h1[3];
-    if (HALO && remote) load_half<P>(h0, h1, halo, fs, f);
-    else load_project<P, MU, S>(h0, h1, in, Vh, nb);
-    hop_apply<P, D, MU, S, LF>(acc, h0, h1, links, Vh, li, cross, ph);
+    if (HALO && remote) {
+        cx<T> h0[3], h1[3];
+        load_half<P>(h0, h1, halo, fs, f);
+        hop_apply<P, D, MU, S, LF>(acc, h0, h1, links, Vh, li, cross, ph);
+    } else {  // the undivided kernel's own hop (its load schedule and arithmetic)
+        hop_one<P, D, MU, S, LF>(acc, in, Vh, nb, links, Vh, (int)li, cross, ph);
+    }
 }
 
 // acc = H in at block site i: like hop_site, with the hops in `remote` read
@@ -357,7 +363,7 @@ struct wl_dd_s {
     // per-block local sums of the reductions (3 doubles per right-hand side)
     double* loc = nullptr;
     int loc_rhs = 0;
-    int direct = 0;  // 1: the pack writes straight into held neighbours' halos (no copy)
+    int direct = 0;  // 1: the pack writes straight into held neighbours' halos (no copy kernel)
     cudaStream_t comm = nullptr;
     cudaEvent_t ev_packed = nullptr, ev_exchanged = nullptr;
     // reduction partials of all blocks and the per-block local sums

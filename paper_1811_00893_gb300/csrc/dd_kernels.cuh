@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(kDDBlock, (MinBlocks<P, DOT>::value * 2)) dd_h
     const long long j = (long long)(blockIdx.x - pidx * A.blocks_per_parity) * kDDBlock + threadIdx.x;
     T part[3] = {0, 0, 0};
     if (j < A.nsites) {
-        const int i = A.sites[j];
+        const int i = A.sites ? A.sites[j] : (int)(A.site0 + j);
         const int p = A.parity0 + pidx;
         int c[4], xh, nb[8];
         half_coords(A.g, p, i, c, xh);

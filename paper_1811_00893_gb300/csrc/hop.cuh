@@ -71,11 +71,15 @@ __device__ __forceinline__ void reconstruct(cx<T> (&acc)[12], int a, cx<T> u0, c
     }
 }
 
-// w0 h0 + w1 h1 + w2 h2 (one row of the SU(3) matrix-vector product)
+// w0 h0 + w1 h1 + w2 h2 (one row of the SU(3) matrix-vector product).  The
+// first product is written with explicit fused multiply-adds, like the two
+// after it (cmac), so that the compiler has no contraction left to choose:
+// every kernel that inlines it rounds alike (the decomposed kernels rely on
+// this to reproduce the undivided result bit for bit).
 template <typename T>
 __device__ __forceinline__ cx<T> dot3(cx<T> w0, cx<T> w1, cx<T> w2, const cx<T> (&h)[3])
 {
-    cx<T> u = w0 * h[0];
+    cx<T> u = {fma(w0.re, h[0].re, -(w0.im * h[0].im)), fma(w0.re, h[0].im, w0.im * h[0].re)};
     cmac(u, w1, h[1]);
     cmac(u, w2, h[2]);
     return u;
