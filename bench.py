@@ -599,7 +599,7 @@ def measure_single(wl, rank, world, local, steps, warmup, *, e2e=True, r12=True,
         out["cpu_baseline"] = oracle_sample(wl, U_host, b_host, cpu_seconds, F_host,
                                             iters_to_tol=out["solve"]["fp64_iters"])
         out["cpu_baseline"]["oracle_D"] = oracle_d_gflops(wl, U_host, b_host)
-    elif cpu:
+    else:
         out["cpu_baseline"] = None
     if oracle_items and rank == 0 and F_host is None:
         out["oracle_solve"] = oracle_solve(wl, U_host, b_host, nrhs_total=wl.nrhs)

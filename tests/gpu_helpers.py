@@ -12,14 +12,15 @@ PRECS = {"f64": wilson.WL_F64, "f32": wilson.WL_F32, "f16": wilson.WL_F16,
          "df64": wilson.WL_DF64}
 
 # Relative L2 tolerances against the FP64 oracle.  FP64 and FP32 are the
-# stated targets; FP16 storage: per-component rounding <= 2^-12 of the site
-# scale (<= 2^-12 sqrt(24) = 1.2e-3 relative per spinor), link entries
-# <= 2^-12 absolute (<= 7.4e-4 relative per 3x3 product), and the stored
-# output another 1.2e-3; errors of the eight hops add incoherently, so the
-# bound is taken as 3e-3.  df64 (hi + lo FP32 pairs): inputs carry <= 2^-48
-# relative rounding, each df64 add or multiply <= 2^-44 (5.7e-14), and an
-# output component takes ~100 dependent operations, so <= 5.7e-12; 1e-11.
-TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 3e-3, "df64": 1e-11}
+# stated targets.  FP16 storage: test_gpu_parity.test_fp16_error_margins
+# measures the hopping term, D and M_ee in FP16 on every parity lattice
+# (Haar and smooth links, both parities and signs): the worst relative error
+# is 3.5e-4 (the per-component binary16 rounding, 2^-12 of the site scale,
+# over 24 components and eight hops adds incoherently to ~3e-4); the bound is
+# twice that.  df64 (hi + lo FP32 pairs): inputs carry <= 2^-48 relative
+# rounding, each df64 add or multiply <= 2^-44 (5.7e-14), and an output
+# component takes ~100 dependent operations, so <= 5.7e-12; 1e-11.
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 7e-4, "df64": 1e-11}
 
 
 def rel(a, b) -> float:

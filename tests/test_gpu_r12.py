@@ -3,7 +3,7 @@
 With the flag the FP32 / FP16 hopping kernels read two rows of each SU(3)
 link and rebuild the third from unitarity, and apply the boundary phases on
 the fly; results must match the FP64 oracle to the same tolerances as the full
-links (FP32 1e-5: the rebuilt row carries FP32 rounding, ~1e-7; FP16 3e-3).
+links (FP32 1e-5: the rebuilt row carries FP32 rounding, ~1e-7; FP16 7e-4).
 Twisted complex phases and L = 2 extents exercise the on-the-fly phases.
 """
 import numpy as np
