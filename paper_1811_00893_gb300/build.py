@@ -51,8 +51,8 @@ def flags(extra=()):
             "-I", INCLUDE, "-I", CSRC, *extra]
 
 
-def compile_unit(src: str, extra=()) -> str:
-    obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+def compile_unit(src: str, extra=(), obj_dir: str = OBJ) -> str:
+    obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
     cmd = [nvcc(), *flags(extra), "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -60,22 +60,26 @@ def compile_unit(src: str, extra=()) -> str:
     return obj
 
 
-def build(force: bool = False, extra=(), verbose: bool = False) -> str:
-    """Compile every translation unit and link libwilson.so; returns its path."""
-    if not force and not extra and up_to_date():
+def build(force: bool = False, extra=(), verbose: bool = False, out_dir: str = None) -> str:
+    """Compile every translation unit and link libwilson.so; returns its path.
+    With out_dir (and build flags in `extra`, e.g. a build variant), objects
+    and library go there and the default library is left alone."""
+    lib = os.path.join(out_dir, "libwilson.so") if out_dir else LIB
+    obj_dir = os.path.join(out_dir, "_build") if out_dir else OBJ
+    if not out_dir and not force and not extra and up_to_date():
         return LIB
-    os.makedirs(OBJ, exist_ok=True)
+    os.makedirs(obj_dir, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 2)) as ex:
-        objs = list(ex.map(lambda s: compile_unit(s, extra), sources()))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: compile_unit(s, extra, obj_dir), sources()))
+    tmp = lib + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -66,16 +66,19 @@ LIB_PATH = _build.LIB
 
 
 def load() -> ctypes.CDLL:
-    """Load libwilson.so (building it first if its sources are newer)."""
+    """Load libwilson.so (building it first if its sources are newer).  The
+    environment variable WL_LIBRARY names another build of it to load instead
+    (a build variant; it is not rebuilt)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        if not _build.up_to_date():
+        path = os.environ.get("WL_LIBRARY") or LIB_PATH
+        if path == LIB_PATH and not _build.up_to_date():
             _build.build()
-        if not os.path.exists(LIB_PATH):
-            raise ImportError(f"CUDA library {LIB_PATH} is missing; run __graft_entry__.build()")
-        lib = ctypes.CDLL(LIB_PATH)
+        if not os.path.exists(path):
+            raise ImportError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
         P, I, D, LL, SZ = (ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
                            ctypes.c_size_t)
         sig = {
