@@ -251,7 +251,11 @@ int wilson_solve(wl_gauge g, double* x, const double* b, int nrhs, const wl_solv
  * 1 <= nlat <= 64, 1 <= nrhs[l] <= 32, even-odd systems only (p->eo = 1),
  * each gauge object at most once; WL_ERR_ARG otherwise.  A gauge object
  * with a clover term contributes D_clov.  info receives sum(nrhs) entries,
- * lattice by lattice.  Synchronises the stream. */
+ * lattice by lattice.  The device description of a batch is cached for the
+ * set of gauge objects (the 8 most recent sets), so callers alternating
+ * between batches do not rebuild it; a gauge object's destruction drops the
+ * descriptions that include it.  Calls must not overlap on the same gauge
+ * objects (as for wilson_solve).  Synchronises the stream. */
 int wilson_solve_batch(int nlat, const wl_gauge* gs, double* const* x, const double* const* b,
                        const int* nrhs, const wl_solve_params* p, wl_solve_info* info,
                        void* stream);

@@ -15,6 +15,7 @@
 //   are inactive and the batched kernels skip them.
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <mutex>
 
 #include "hop.cuh"
@@ -304,8 +305,12 @@ struct BatchCtx {
     }
 };
 
+// Device descriptions of recent batches, most recently used last, found again
+// by their gauge objects and workspaces: callers that alternate between
+// batches reuse theirs instead of rebuilding (and synchronising the device).
 static std::mutex g_batch_mu;
-static BatchCtx* g_batch = nullptr;  // the last batch's context, reused while it matches
+static std::vector<std::shared_ptr<BatchCtx>> g_batches;
+static const size_t kBatchCache = 8;
 
 BatchArgs args_of(const BatchCtx& C)
 {
@@ -493,7 +498,7 @@ static int run_batch_chunk(BatchCtx& C, int k, bool use_graph, cudaStream_t s)
 }
 
 // Build (or reuse) the device description of the batch.
-static int batch_context(const std::vector<SolveState>& st, int P, BatchCtx** out)
+static int batch_context(const std::vector<SolveState>& st, int P, std::shared_ptr<BatchCtx>* out)
 {
     std::vector<BLat> lats(st.size());
     int item = 0, nsys = 0, max_chunks = 1;
@@ -534,16 +539,22 @@ static int batch_context(const std::vector<SolveState>& st, int P, BatchCtx** ou
                   L.nrhs * ((2 + 4 + 2 + 4 + 12) * (double)spinor_field_bytes(P, 1) +
                             2.0 * spinor_field_bytes(S.w->xlo_prec, 1)));
     }
-    BatchCtx* C = g_batch;
-    const bool same = C && C->P == P && C->lats_h.size() == lats.size() &&
-                      std::memcmp(C->lats_h.data(), lats.data(), sizeof(BLat) * lats.size()) == 0;
-    if (same) {
-        *out = C;
-        return WL_OK;
+    {
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        for (size_t k = 0; k < g_batches.size(); ++k) {
+            BatchCtx* C = g_batches[k].get();
+            if (C->P == P && C->lats_h.size() == lats.size() &&
+                std::memcmp(C->lats_h.data(), lats.data(), sizeof(BLat) * lats.size()) == 0) {
+                std::shared_ptr<BatchCtx> keep = g_batches[k];
+                g_batches.erase(g_batches.begin() + (long)k);
+                g_batches.push_back(keep);
+                *out = keep;
+                return WL_OK;
+            }
+        }
     }
-    WL_CUDA(cudaDeviceSynchronize());
-    delete g_batch;
-    g_batch = C = new BatchCtx();
+    std::shared_ptr<BatchCtx> fresh = std::make_shared<BatchCtx>();
+    BatchCtx* C = fresh.get();
     C->lats_h = lats;
     for (const SolveState& S : st) C->gs.push_back(S.g);
     C->P = P;
@@ -570,7 +581,14 @@ static int batch_context(const std::vector<SolveState>& st, int P, BatchCtx** ou
     WL_CUDA(cudaMalloc((void**)&C->red.ticket, sizeof(unsigned) * nsys));
     WL_CUDA(cudaMemset(C->red.ticket, 0, sizeof(unsigned) * nsys));
     C->red.max_blocks = max_chunks;
-    *out = C;
+    {
+        // the least recently used context leaves the cache (its device memory
+        // is freed once no solve uses it any more)
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        if (g_batches.size() >= kBatchCache) g_batches.erase(g_batches.begin());
+        g_batches.push_back(fresh);
+    }
+    *out = fresh;
     return WL_OK;
 }
 
@@ -578,14 +596,15 @@ static int batch_context(const std::vector<SolveState>& st, int P, BatchCtx** ou
 
 using namespace wl;
 
-// Drop a cached batch context that refers to a gauge object being destroyed.
+// Drop the cached batch contexts that refer to a gauge object being destroyed
+// (the caller has synchronised the device).
 void batch_forget(wl_gauge g)
 {
     std::lock_guard<std::mutex> lock(g_batch_mu);
-    if (g_batch && std::find(g_batch->gs.begin(), g_batch->gs.end(), g) != g_batch->gs.end()) {
-        cudaDeviceSynchronize();
-        delete g_batch;
-        g_batch = nullptr;
+    for (size_t k = 0; k < g_batches.size();) {
+        const auto& gs = g_batches[k]->gs;
+        if (std::find(gs.begin(), gs.end(), g) != gs.end()) g_batches.erase(g_batches.begin() + (long)k);
+        else ++k;
     }
 }
 
@@ -603,12 +622,12 @@ extern "C" int wilson_solve_batch(int nlat, const wl_gauge* gs, double* const* x
         for (int m = 0; m < l; ++m)
             if (gs[m] == gs[l]) return set_error(WL_ERR_ARG, "a gauge object appears twice in the batch");
     }
-    std::lock_guard<std::mutex> lock(g_batch_mu);
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<SolveState> st(nlat);
     for (int l = 0; l < nlat; ++l) WL_TRY(st[l].begin(gs[l], x[l], b[l], nrhs[l], prm, s));
-    BatchCtx* C = nullptr;
-    WL_TRY(batch_context(st, prm->inner, &C));
+    std::shared_ptr<BatchCtx> ctx;
+    WL_TRY(batch_context(st, prm->inner, &ctx));
+    BatchCtx* C = ctx.get();
     enum { PLAN, ITER, FINAL, DONE };
     std::vector<int> phase(nlat, PLAN);
     const int chunk = st[0].chunk;

@@ -99,3 +99,24 @@ def test_uneven_batch_workload():
     finally:
         for c in cases:
             c.close()
+
+
+def test_alternating_batches_keep_their_contexts():
+    """Two callers alternating between two batches (and a batch sharing a
+    lattice with another): each batch finds its cached device description
+    again, and every solve reaches the oracle residual."""
+    cases, bs = make_batch(SMALL)
+    try:
+        groups = [[0, 1], [2, 3], [1, 2]]
+        p = wilson.solve_params(tol=TOL, eo=True, inner=wilson.WL_F32, graph_iters=4)
+        for rep in range(3):
+            for grp in groups:
+                cs = [cases[i] for i in grp]
+                bb = [bs[i] for i in grp]
+                xs = [torch.zeros_like(b) for b in bb]
+                rc, infos = wilson.wilson_solve_batch([c.g.handle for c in cs], xs, bb,
+                                                      [b.shape[0] for b in bb], p)
+                check(cs, bb, xs, infos)
+    finally:
+        for c in cases:
+            c.close()
