@@ -304,9 +304,11 @@ int wl_dd_create(wl_dd* dd, const wl_lattice* lat, const int grid[4], const doub
  * end.  Faces are the spin-projected half spinors of a block's x_mu = 0
  * (side 0, sent to the backward neighbour) or x_mu = L_mu - 1 (side 1, sent
  * to the forward neighbour) sites, 6 complex per face site in the
- * arithmetic precision (FP64 / df64: 96 B, FP32 / FP16: 48 B per site),
- * all right-hand sides back to back.  Layout of one right-hand side's face
- * in FP64: 6 planes of one complex double per face site, plane 3 s + c
+ * arithmetic precision (FP64 / df64: 96 B, FP32: 48 B per site; FP16
+ * storage: 48 B of the projection of the stored 16-bit values, not yet
+ * multiplied by the site's norm, then the FP32 norms of the face sites, padded
+ * to a multiple of 16 B), all right-hand sides back to back.  Layout of one
+ * right-hand side's face in FP64: 6 planes of one complex double per face site, plane 3 s + c
  * holding spin row s (0 or 1) and colour c of (1 - gamma_mu) psi (side 0) or
  * (1 + gamma_mu) psi (side 1) at that site (the dagger flips the signs); the
  * two rows determine the other two.  Face sites are ordered by their half

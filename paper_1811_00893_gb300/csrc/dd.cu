@@ -251,7 +251,6 @@ static int ensure_loc(wl_dd dd, int nrhs)
 void dd_segments(const Geom& g, int cut, int P, int nrhs, int np, long long (&hoff)[2][4][2], DDSeg (&seg)[12],
                  int& nseg, long long& total, long long& bytes)
 {
-    const long long hsb = (long long)halo_site_bytes(P);
     std::memset(hoff, 0, sizeof hoff);
     nseg = 0;
     total = 0;
@@ -262,7 +261,7 @@ void dd_segments(const Geom& g, int cut, int P, int nrhs, int np, long long (&ho
                 for (int side = 0; side < 2; ++side) {
                     const long long fs = g.Vh / g.L[mu];
                     hoff[k][mu][side] = bytes;
-                    bytes += fs * hsb * nrhs;
+                    bytes += halo_face_bytes(P, fs) * nrhs;
                     seg[nseg++] = {k, mu, side, total, fs};
                     total += fs;
                 }
@@ -281,7 +280,6 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
     const int lf = (P == WL_F32 || P == WL_F16) && dd->dom[0]->links_r12[P][0] && !r12_off ? 1 : 0;
     const int np = h.nparity, nrhs = h.nrhs;
     const Geom& g = dd->gloc;
-    const long long hsb = (long long)halo_site_bytes(P);
 
     // halo segments of (launch parity, mu, side), all right-hand sides each
     long long hoff[2][4][2];
@@ -387,7 +385,7 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
         }
         const dim3 grid((unsigned)((total + kDDBlock - 1) / kDDBlock), (unsigned)nrhs, (unsigned)dd->ndom);
         DDKernels<0>::pack(P, h.dagger != 0, PA, grid, dd->comm);
-        WL_CHECK_LAUNCH((double)nrhs * dd->ndom * total * (sb + hsb));
+        WL_CHECK_LAUNCH((double)nrhs * dd->ndom * total * (sb + 16 * halo_planes(P) + (P == WL_F16 ? 4 : 0)));
         // 2. exchange: device copies between held blocks, messages through the
         // transport for the rest
         dd->msgs.clear();
@@ -397,7 +395,7 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
             for (int k = 0; k < nseg; ++k) {
                 const DDSeg& S = seg[k];
                 const long long o = hoff[S.pidx][S.mu][S.side];
-                const size_t bytes = (size_t)(S.count * hsb * nrhs);
+                const size_t bytes = (size_t)(halo_face_bytes(P, S.count) * nrhs);
                 const int to = dd->peer[d][S.mu][S.side], from = dd->peer[d][S.mu][1 - S.side];
                 if (dd->local_of[to] < 0 || route_all) {
                     dd->msgs.push_back({1, dd->gid[d], to, 12 * to + seg_code(S), (size_t)o, bytes, dd->send[d] + o});
@@ -636,14 +634,13 @@ extern "C" int wl_dd_plan(const int* dims, const int* grid, int block, wl_prec p
     int nseg = 0;
     long long total = 0, bytes = 0;
     dd_segments(make_geom(loc), cut, prec, nrhs, nparity, hoff, seg, nseg, total, bytes);
-    const long long hsb = (long long)halo_site_bytes(prec);
     int c[4];
     block_coords(grid, block, c);
     int n = 0;
     for (int k = 0; k < nseg; ++k) {
         const DDSeg& S = seg[k];
         const size_t o = (size_t)hoff[S.pidx][S.mu][S.side];
-        const size_t b = (size_t)(S.count * hsb * nrhs);
+        const size_t b = (size_t)(halo_face_bytes(prec, S.count) * nrhs);
         const int to = block_peer(grid, c, S.mu, S.side), from = block_peer(grid, c, S.mu, 1 - S.side);
         const wl_dd_msg m[2] = {{1, block, to, 12 * to + seg_code(S), o, b, nullptr},
                                 {0, block, from, 12 * block + seg_code(S), o, b, nullptr}};

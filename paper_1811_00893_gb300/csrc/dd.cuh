@@ -36,21 +36,29 @@ static constexpr int kMaxDomains = 16;  // blocks one process holds (one launch 
 // Halo planes: a projected half spinor is 6 complex numbers, stored as 16-byte
 // planes over the face sites (3 float4 of two complex in FP32 arithmetic, 6
 // double2 in FP64, 6 float4 hi/lo pairs in df64).  FP16 storage computes in
-// FP32, so its halo is FP32: the boundary sites then see exactly the half
-// spinor the undivided kernel would have formed.
+// FP32, so its halo is FP32, and like the undivided FP16 kernel it keeps the
+// half spinor of the neighbour's stored values unscaled, followed by a plane
+// of the neighbour's FP32 norms: the boundary sites then see exactly the
+// operands the undivided kernel would have formed.
 __host__ __device__ constexpr int halo_planes(int P) { return (P == WL_F32 || P == WL_F16) ? 3 : 6; }
-inline size_t halo_site_bytes(int P) { return 16 * (size_t)halo_planes(P); }
+// Bytes of one right-hand side's face of fs sites (a multiple of 16)
+__host__ __device__ constexpr long long halo_face_bytes(int P, long long fs)
+{
+    return 16 * halo_planes(P) * fs + (P == WL_F16 ? 16 * ((fs + 3) / 4) : 0);
+}
 
+// nrm: the FP16 neighbour's per-site norm (unused for the other types)
 template <int P>
 __device__ __forceinline__ void store_half(char* base, long long fs, long long f,
                                            const cx<typename Prec<P>::real> (&h0)[3],
-                                           const cx<typename Prec<P>::real> (&h1)[3])
+                                           const cx<typename Prec<P>::real> (&h1)[3], float nrm)
 {
     if constexpr (P == WL_F32 || P == WL_F16) {
         float4* q = (float4*)base;
         q[0 * fs + f] = make_float4(h0[0].re, h0[0].im, h0[1].re, h0[1].im);
         q[1 * fs + f] = make_float4(h0[2].re, h0[2].im, h1[0].re, h1[0].im);
         q[2 * fs + f] = make_float4(h1[1].re, h1[1].im, h1[2].re, h1[2].im);
+        if constexpr (P == WL_F16) ((float*)(q + 3 * fs))[f] = nrm;
     } else if constexpr (P == WL_F64) {
         double2* q = (double2*)base;
 #pragma unroll
@@ -70,8 +78,9 @@ __device__ __forceinline__ void store_half(char* base, long long fs, long long f
 
 template <int P>
 __device__ __forceinline__ void load_half(cx<typename Prec<P>::real> (&h0)[3], cx<typename Prec<P>::real> (&h1)[3],
-                                          const char* base, long long fs, long long f)
+                                          float& nrm, const char* base, long long fs, long long f)
 {
+    nrm = 1.0f;
     if constexpr (P == WL_F32 || P == WL_F16) {
         const float4* q = (const float4*)base;
         const float4 a = __ldg(q + f), b = __ldg(q + fs + f), c = __ldg(q + 2 * fs + f);
@@ -81,6 +90,7 @@ __device__ __forceinline__ void load_half(cx<typename Prec<P>::real> (&h0)[3], c
         h1[0] = {b.z, b.w};
         h1[1] = {c.x, c.y};
         h1[2] = {c.z, c.w};
+        if constexpr (P == WL_F16) nrm = __ldg((const float*)(q + 3 * fs) + f);
     } else if constexpr (P == WL_F64) {
         const double2* q = (const double2*)base;
 #pragma unroll
@@ -211,8 +221,9 @@ __device__ __forceinline__ void dd_hop_one(cx<typename Prec<P>::real> (&acc)[12]
     using T = typename Prec<P>::real;
     if (HALO && remote) {
         cx<T> h0[3], h1[3];
-        load_half<P>(h0, h1, halo, fs, f);
-        hop_apply<P, D, MU, S, LF>(acc, h0, h1, links, Vh, li, cross, ph);
+        float nrm;
+        load_half<P>(h0, h1, nrm, halo, fs, f);
+        hop_apply<P, D, MU, S, LF>(acc, h0, h1, links, Vh, li, cross, ph, nrm);
     } else {  // the undivided kernel's own hop (its load schedule and arithmetic)
         hop_one<P, D, MU, S, LF>(acc, in, Vh, nb, links, Vh, (int)li, cross, ph);
     }
@@ -234,7 +245,8 @@ __device__ __forceinline__ void dd_hop_site(cx<typename Prec<P>::real> (&acc)[12
         for (int d = 0; d < 8; ++d) {
             cx<T> h0[3], h1[3];
             if (HALO && ((remote >> d) & 1)) {
-                load_half<P>(h0, h1, halo[d >> 1][d & 1], A.fs[d >> 1], f[d >> 1]);
+                float unused;
+                load_half<P>(h0, h1, unused, halo[d >> 1][d & 1], A.fs[d >> 1], f[d >> 1]);
             } else {
                 cx<T> q[12];
                 load_spinor_ro<P>(q, in, Vh, nb[d]);

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kDDBlock, (MinBlocks<P, DOT>::value * 2)) dd_h
             for (int mu = 1; mu < 4; ++mu)
                 if (A.fs[mu]) {
                     f[mu] = face_index(A.g, mu, c, xh);
-                    const long long seg_rs = A.fs[mu] * (long long)(16 * halo_planes(P));
+                    const long long seg_rs = halo_face_bytes(P, A.fs[mu]);
                     halo[mu][0] = D.halo + A.hoff[pidx][mu][0] + rhs * seg_rs;
                     halo[mu][1] = D.halo + A.hoff[pidx][mu][1] + rhs * seg_rs;
                 }
@@ -66,6 +66,16 @@ __global__ void __launch_bounds__(kDDBlock, (MinBlocks<P, DOT>::value * 2)) dd_h
     }
 }
 
+// The half spinor a face carries: FP16 storage unscaled with its norm (the
+// operands of the undivided FP16 hop), the others as load_project forms them.
+template <int P, int MU, int S>
+__device__ __forceinline__ void pack_project(cx<typename Prec<P>::real> (&h0)[3], cx<typename Prec<P>::real> (&h1)[3],
+                                             float& nrm, const void* in, long long Vh, int i)
+{
+    if constexpr (P == WL_F16) load_project_f16<MU, S>(h0, h1, nrm, in, Vh, i);
+    else load_project<P, MU, S>(h0, h1, in, Vh, i);
+}
+
 // The spin-projected half spinors of the faces a neighbouring block needs.
 template <int P, bool DAG>
 __global__ void __launch_bounds__(kDDBlock) dd_pack_kernel(const DDPackArgs A)
@@ -85,6 +95,7 @@ __global__ void __launch_bounds__(kDDBlock) dd_pack_kernel(const DDPackArgs A)
     const int i = (int)(below + xmu * s_mu + above * s_mu * A.g.L[S.mu]);
     const char* in = A.in[dom][S.pidx] + rhs * A.rs_in;
     cx<T> h0[3], h1[3];
+    float nrm = 1.0f;
     const int d = 2 * S.mu + S.side;  // the hop of the receiving block
     if constexpr (P == WL_DF64) {
         cx<T> q[12];
@@ -94,16 +105,16 @@ __global__ void __launch_bounds__(kDDBlock) dd_pack_kernel(const DDPackArgs A)
         constexpr int F = DAG ? +1 : -1;  // forward projector sign
         constexpr int B = -F;
         switch (d) {
-            case 2: load_project<P, 1, F>(h0, h1, in, A.g.Vh, i); break;
-            case 3: load_project<P, 1, B>(h0, h1, in, A.g.Vh, i); break;
-            case 4: load_project<P, 2, F>(h0, h1, in, A.g.Vh, i); break;
-            case 5: load_project<P, 2, B>(h0, h1, in, A.g.Vh, i); break;
-            case 6: load_project<P, 3, F>(h0, h1, in, A.g.Vh, i); break;
-            default: load_project<P, 3, B>(h0, h1, in, A.g.Vh, i); break;
+            case 2: pack_project<P, 1, F>(h0, h1, nrm, in, A.g.Vh, i); break;
+            case 3: pack_project<P, 1, B>(h0, h1, nrm, in, A.g.Vh, i); break;
+            case 4: pack_project<P, 2, F>(h0, h1, nrm, in, A.g.Vh, i); break;
+            case 5: pack_project<P, 2, B>(h0, h1, nrm, in, A.g.Vh, i); break;
+            case 6: pack_project<P, 3, F>(h0, h1, nrm, in, A.g.Vh, i); break;
+            default: pack_project<P, 3, B>(h0, h1, nrm, in, A.g.Vh, i); break;
         }
     }
-    const long long seg_rs = S.count * (long long)(16 * halo_planes(P));
-    store_half<P>(A.dst[dom][S.mu][S.side] + A.hoff[S.pidx][S.mu][S.side] + rhs * seg_rs, S.count, f, h0, h1);
+    store_half<P>(A.dst[dom][S.mu][S.side] + A.hoff[S.pidx][S.mu][S.side] + rhs * halo_face_bytes(P, S.count),
+                  S.count, f, h0, h1, nrm);
 }
 
 // Launchers of one link format (LF = 1 exists for FP32 / FP16 only).

@@ -336,6 +336,24 @@ __device__ __forceinline__ void load_spinor_ro_f16_unscaled(cx<float> (&v)[12], 
     }
 }
 
+// The same with plain loads, for the epilogue's operands (which may be the
+// field the launch writes)
+__device__ __forceinline__ void load_spinor_f16_unscaled(cx<float> (&v)[12], float& nrm, const void* base,
+                                                         long long Vh, long long i)
+{
+    const uint4* p = (const uint4*)base;
+    nrm = ((const float*)(p + 3 * Vh))[i] * kSpin16Unit;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const uint4 t = p[k * Vh + i];
+        const float2 a = s16_dec(t.x), b = s16_dec(t.y), c = s16_dec(t.z), d = s16_dec(t.w);
+        v[4 * k + 0] = {a.x, a.y};
+        v[4 * k + 1] = {b.x, b.y};
+        v[4 * k + 2] = {c.x, c.y};
+        v[4 * k + 3] = {d.x, d.y};
+    }
+}
+
 // FP16 half h plus the FP32 value c, rounded once in FP32: the result of
 // converting h (exactly) and adding in FP32, as one mixed-precision add
 // (sm_100 and later) instead of a conversion and an add.
@@ -380,6 +398,36 @@ __device__ __forceinline__ void project_f16(cx<float> (&h0)[3], cx<float> (&h1)[
     }
 }
 
+// The projected half spinor of the FP16 neighbour spinor at index nb, not
+// yet multiplied by the neighbour's per-site norm, which is returned in nrm:
+// the hop applies it in its reconstruction (one FFMA per value instead of a
+// multiply here and an add there).
+template <int MU, int S>
+__device__ __forceinline__ void load_project_f16(cx<float> (&h0)[3], cx<float> (&h1)[3], float& nrm, const void* in,
+                                                 long long Vh, int nb)
+{
+#if WL_F16_MIXED_ADD && !WL_SPINOR16_FIXED
+    unsigned w[12];
+    {
+        const uint4* p = (const uint4*)in;
+        nrm = __ldg((const float*)(p + 3 * Vh) + nb);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint4 t = __ldg(p + k * Vh + nb);
+            w[4 * k + 0] = t.x;
+            w[4 * k + 1] = t.y;
+            w[4 * k + 2] = t.z;
+            w[4 * k + 3] = t.w;
+        }
+    }
+    project_f16<MU, S>(h0, h1, w);
+#else
+    cx<float> q[12];
+    load_spinor_ro_f16_unscaled(q, nrm, in, Vh, nb);
+    project<MU, S>(h0, h1, q);
+#endif
+}
+
 // the projected half spinor of the neighbour spinor at index nb
 template <int P, int MU, int S>
 __device__ __forceinline__ void load_project(cx<typename Prec<P>::real> (&h0)[3],
@@ -387,37 +435,59 @@ __device__ __forceinline__ void load_project(cx<typename Prec<P>::real> (&h0)[3]
                                              long long Vh, int nb)
 {
     using T = typename Prec<P>::real;
-    cx<T> q[12];
     if constexpr (P == WL_F16) {
         float nrm;
-#if WL_F16_MIXED_ADD && !WL_SPINOR16_FIXED
-        (void)q;
-        unsigned w[12];
-        {
-            const uint4* p = (const uint4*)in;
-            nrm = __ldg((const float*)(p + 3 * Vh) + nb);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const uint4 t = __ldg(p + k * Vh + nb);
-                w[4 * k + 0] = t.x;
-                w[4 * k + 1] = t.y;
-                w[4 * k + 2] = t.z;
-                w[4 * k + 3] = t.w;
-            }
-        }
-        project_f16<MU, S>(h0, h1, w);
-#else
-        load_spinor_ro_f16_unscaled(q, nrm, in, Vh, nb);
-        project<MU, S>(h0, h1, q);
-#endif
+        load_project_f16<MU, S>(h0, h1, nrm, in, Vh, nb);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             h0[c] = nrm * h0[c];
             h1[c] = nrm * h1[c];
         }
     } else {
+        cx<T> q[12];
         load_spinor_ro<P>(q, in, Vh, nb);
         project<MU, S>(h0, h1, q);
+    }
+}
+
+// acc += s i^K u (K = 0: u, 1: i u, 2: -u, 3: -i u), as two FFMAs
+template <int K>
+__device__ __forceinline__ void fma_ik(cx<float>& acc, float s, cx<float> u)
+{
+    if constexpr (K == 0) {
+        acc.re = fmaf(s, u.re, acc.re);
+        acc.im = fmaf(s, u.im, acc.im);
+    } else if constexpr (K == 1) {
+        acc.re = fmaf(-s, u.im, acc.re);
+        acc.im = fmaf(s, u.re, acc.im);
+    } else if constexpr (K == 2) {
+        acc.re = fmaf(-s, u.re, acc.re);
+        acc.im = fmaf(-s, u.im, acc.im);
+    } else {
+        acc.re = fmaf(s, u.im, acc.re);
+        acc.im = fmaf(-s, u.re, acc.im);
+    }
+}
+
+// reconstruct() of s (u0, u1): the four spin rows of s (1 + S gamma_mu) W psi
+// added with FFMAs (the FP16 hops pass the neighbour's norm as s)
+template <int MU, int S>
+__device__ __forceinline__ void reconstruct_scaled(cx<float> (&acc)[12], int a, cx<float> u0, cx<float> u1, float s)
+{
+    fma_ik<0>(acc[a], s, u0);
+    fma_ik<0>(acc[3 + a], s, u1);
+    if constexpr (MU == 0) {  // rows 2, 3 += -S i (u1, u0)
+        fma_ik<(S > 0 ? 3 : 1)>(acc[6 + a], s, u1);
+        fma_ik<(S > 0 ? 3 : 1)>(acc[9 + a], s, u0);
+    } else if constexpr (MU == 1) {  // rows 2, 3 += (S u1, -S u0)
+        fma_ik<(S > 0 ? 0 : 2)>(acc[6 + a], s, u1);
+        fma_ik<(S > 0 ? 2 : 0)>(acc[9 + a], s, u0);
+    } else if constexpr (MU == 2) {  // rows 2, 3 += (-S i u0, S i u1)
+        fma_ik<(S > 0 ? 3 : 1)>(acc[6 + a], s, u0);
+        fma_ik<(S > 0 ? 1 : 3)>(acc[9 + a], s, u1);
+    } else {  // rows 2, 3 += S (u0, u1)
+        fma_ik<(S > 0 ? 0 : 2)>(acc[6 + a], s, u0);
+        fma_ik<(S > 0 ? 0 : 2)>(acc[9 + a], s, u1);
     }
 }
 
@@ -427,7 +497,28 @@ __device__ __forceinline__ void hop_one(cx<typename Prec<P>::real> (&acc)[12], c
                                         int li, unsigned cross, const cx<float>* ph)
 {
     using T = typename Prec<P>::real;
-    if constexpr (LF == 1) {
+    if constexpr (P == WL_F16) {  // the neighbour's norm enters the reconstruction
+        cx<T> h0[3], h1[3], W[9];
+        float nrm;
+        load_project_f16<MU, S>(h0, h1, nrm, in, Vh, nb);
+        if constexpr (LF == 1) {
+            if (cross & (1u << D)) {  // boundary phase: phi forward, conj(phi) backward
+                const cx<T> f = (D & 1) ? conj(ph[MU]) : ph[MU];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    h0[c] = f * h0[c];
+                    h1[c] = f * h1[c];
+                }
+            }
+            load_link_r12<P>(W, links, lVh, D, li);
+        } else {
+            load_link<P>(W, links, lVh, D, li);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            reconstruct_scaled<MU, S>(acc, a, dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h0),
+                                      dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h1), nrm);
+    } else if constexpr (LF == 1) {
         cx<T> h0[3], h1[3], W[9];
         load_project<P, MU, S>(h0, h1, in, Vh, nb);
         if (cross & (1u << D)) {  // boundary phase: phi forward, conj(phi) backward
@@ -452,14 +543,6 @@ __device__ __forceinline__ void hop_one(cx<typename Prec<P>::real> (&acc)[12], c
             load_link_row<P>(w, links, lVh, D, li, a);
             reconstruct<MU, S>(acc, a, dot3(w[0], w[1], w[2], h0), dot3(w[0], w[1], w[2], h1));
         }
-    } else if constexpr (P == WL_F16) {
-        cx<T> h0[3], h1[3], W[9];
-        load_project<P, MU, S>(h0, h1, in, Vh, nb);
-        load_link<P>(W, links, lVh, D, li);
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            reconstruct<MU, S>(acc, a, dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h0),
-                               dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h1));
     } else {  // FP32 (df64 takes hop_site_loop instead)
         cx<T> q[12], W[9];
         load_spinor_ro<P>(q, in, Vh, nb);
@@ -470,13 +553,14 @@ __device__ __forceinline__ void hop_one(cx<typename Prec<P>::real> (&acc)[12], c
 
 // The part of hop_one after the spin projection: given the projected half
 // spinor (h0, h1) of hop D, apply the boundary phase (compressed links), the
-// link and the reconstruction.  The domain-decomposed kernels use it for hops
-// whose half spinor arrives from a neighbouring block, and with load_project
-// for the others; it performs the same operations as hop_one.
+// link and the reconstruction (scaled by the neighbour's norm s for FP16
+// storage, whose h arrive unscaled).  The domain-decomposed kernels use it for
+// hops whose half spinor arrives from a neighbouring block; it performs the
+// same operations as hop_one.
 template <int P, int D, int MU, int S, int LF>
 __device__ __forceinline__ void hop_apply(cx<typename Prec<P>::real> (&acc)[12], cx<typename Prec<P>::real> (&h0)[3],
                                           cx<typename Prec<P>::real> (&h1)[3], const void* links, long long lVh,
-                                          long long li, unsigned cross, const cx<float>* ph)
+                                          long long li, unsigned cross, const cx<float>* ph, float s = 1.0f)
 {
     using T = typename Prec<P>::real;
     if constexpr (LF == 1) {
@@ -488,13 +572,8 @@ __device__ __forceinline__ void hop_apply(cx<typename Prec<P>::real> (&acc)[12],
                 h1[c] = f * h1[c];
             }
         }
-        cx<T> W[9];
-        load_link_r12<P>(W, links, lVh, D, li);
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            reconstruct<MU, S>(acc, a, dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h0),
-                               dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h1));
-    } else if constexpr (P == WL_F64) {
+    }
+    if constexpr (P == WL_F64 && LF == 0) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             cx<T> w[3];
@@ -503,11 +582,17 @@ __device__ __forceinline__ void hop_apply(cx<typename Prec<P>::real> (&acc)[12],
         }
     } else {
         cx<T> W[9];
-        load_link<P>(W, links, lVh, D, li);
+        if constexpr (LF == 1) load_link_r12<P>(W, links, lVh, D, li);
+        else load_link<P>(W, links, lVh, D, li);
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-            reconstruct<MU, S>(acc, a, dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h0),
-                               dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h1));
+        for (int a = 0; a < 3; ++a) {
+            if constexpr (P == WL_F16)
+                reconstruct_scaled<MU, S>(acc, a, dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h0),
+                                          dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h1), s);
+            else
+                reconstruct<MU, S>(acc, a, dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h0),
+                                   dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h1));
+        }
     }
 }
 
@@ -701,16 +786,29 @@ __device__ __forceinline__ void epilogue_ptrs(cx<typename Prec<P>::real> (&acc)[
     const T a = (T)a_;
 #pragma unroll
     for (int c = 0; c < 12; ++c) acc[c] = a * acc[c];
+    // FP16 operands enter unscaled, their per-site norm folded into one FFMA
+    // per value (n = 1 for the other types)
     if (x1) {
         cx<T> x[12];
-        load_spinor<P>(x, x1, Vh, i);
+        T n = (T)1;
+        if constexpr (P == WL_F16) load_spinor_f16_unscaled(x, n, x1, Vh, i);
+        else load_spinor<P>(x, x1, Vh, i);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) acc[c] = acc[c] + x[c];
+        for (int c = 0; c < 12; ++c) {
+            if constexpr (P == WL_F16) acc[c] = {fmaf(n, x[c].re, acc[c].re), fmaf(n, x[c].im, acc[c].im)};
+            else acc[c] = acc[c] + x[c];
+        }
     }
     if (x2) {
         cx<T> x[12];
-        const T b1 = (T)b1_;
-        load_spinor<P>(x, x2, Vh, i);
+        T b1 = (T)b1_;
+        if constexpr (P == WL_F16) {
+            float n;
+            load_spinor_f16_unscaled(x, n, x2, Vh, i);
+            b1 = b1 * n;  // the clover multiply below is linear
+        } else {
+            load_spinor<P>(x, x2, Vh, i);
+        }
         if (CL == kClX2) clover_mul<P>(x, cl, Vh, i);
 #pragma unroll
         for (int c = 0; c < 12; ++c) acc[c] = acc[c] + b1 * x[c];
@@ -720,8 +818,16 @@ __device__ __forceinline__ void epilogue_ptrs(cx<typename Prec<P>::real> (&acc)[
     if (DOT) {
         if (w) {
             cx<T> ww[12];
-            load_spinor<P>(ww, w, Vh, i);
-            site_dots<P>(acc, ww, part);
+            if constexpr (P == WL_F16) {
+                float n;
+                load_spinor_f16_unscaled(ww, n, w, Vh, i);
+                site_dots<P>(acc, ww, part);
+                part[0] *= n;
+                part[1] *= n;
+            } else {
+                load_spinor<P>(ww, w, Vh, i);
+                site_dots<P>(acc, ww, part);
+            }
         } else {
             site_dots<P>(acc, nullptr, part);
         }
