@@ -14,7 +14,9 @@ Reported:
              resident in device memory before the timed region;
   e2e        the same with host (pinned) b and x: H2D and D2H inside each step;
   roofline   the FP32 hopping kernel: its algorithmic bytes over its CUDA-event
-             time inside the timed region, against the measured HBM copy peak;
+             time in the solve (a second pass of the same K solves with an
+             event pair around every hopping launch; the timed region runs
+             without them), against the measured HBM copy peak;
   dslash     the paper's protocol (Sec. 5.4): 1000 back-to-back FP32 hopping
              applications timed with CUDA events (GB/s, GFlop/s at 1320/site);
   solve      mixed-precision vs plain FP64 BiCGStab time to 1e-10;
@@ -67,6 +69,9 @@ def parse_args(argv=None):
                     help="skip the other workloads' sub-records (default: measured after the headline)")
     ap.add_argument("--dims", type=str, default=None,
                     help="override the lattice extents, e.g. 24,24,24,48 (smaller profiling runs)")
+    ap.add_argument("--dd", action="store_true",
+                    help="measure only the decomposed operator and solve (2 and 4 blocks) on the "
+                         "workload's lattice, --steps launches per timing (profiling runs)")
     return ap.parse_args(argv)
 
 
@@ -418,7 +423,6 @@ def measure_single(wl, rank, world, local, steps, warmup, *, e2e=True, r12=True,
     for _ in range(max(3, warmup)):
         rc, info = solve(x, b)
     # ---------------- timed region: K solves, inputs resident in HBM
-    wilson.wl_timing(g.handle, True)
     clk = ClockSampler(gpu_index_for(local)).start()
     l0, b0 = wilson.wl_launch_count(), wilson.wl_algorithmic_bytes()
     barrier(world)
@@ -436,6 +440,18 @@ def measure_single(wl, rank, world, local, steps, warmup, *, e2e=True, r12=True,
     ms_local = e0.elapsed_time(e1)
     launches = wilson.wl_launch_count() - l0
     bytes_local = wilson.wl_algorithmic_bytes() - b0
+    # ---------------- the same K solves again with a CUDA-event pair around
+    # every hopping launch (the kernels' own durations; the records between
+    # launches cost ~2 % of a step, so the timed region above runs without)
+    wilson.wl_timing(g.handle, True)
+    torch.cuda.synchronize()
+    i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    i0.record(stream)
+    for _ in range(steps):
+        solve(x, b)
+    i1.record(stream)
+    torch.cuda.synchronize()
+    ms_instr = i0.elapsed_time(i1)
     wilson.wl_timing(g.handle, False)
     hop_ms, hop_n, hop_bytes = wilson.wl_timing_read(g.handle, P)
     h64_ms, h64_n, h64_bytes = wilson.wl_timing_read(g.handle, wilson.WL_F64)
@@ -558,7 +574,8 @@ def measure_single(wl, rank, world, local, steps, warmup, *, e2e=True, r12=True,
                     "algorithmic_bytes_per_launch": bps * Vh, "avg_us": dslash["us_per_launch"]}
     else:
         traffic = profiled_traffic()
-        roofline = {"kernel": kname + " (all hopping launches of the inner solve)",
+        roofline = {"kernel": kname + " (all hopping launches of the inner solve; per-launch CUDA events "
+                              "in a second pass of the same K solves)",
                     "bound": "hbm", "achieved": achieved, "peak": peak,
                     "peak_kind": peak_kind, "unit": "GB/s",
                     "frac": (achieved / peak) if achieved else None,
@@ -567,8 +584,9 @@ def measure_single(wl, rank, world, local, steps, warmup, *, e2e=True, r12=True,
                     "launches": hop_n,
                     "algorithmic_bytes_per_launch": hop_bytes / max(hop_n, 1),
                     "avg_us": hop_ms * 1e3 / max(hop_n, 1),
-                    "share_of_step": hop_ms / ms_local if ms_local else None,
-                    "f64_hop_share_of_step": h64_ms / ms_local if ms_local else None}
+                    "share_of_step": hop_ms / ms_instr if ms_instr else None,
+                    "f64_hop_share_of_step": h64_ms / ms_instr if ms_instr else None,
+                    "instrumented_ms_per_step": ms_instr / steps}
     mixed_iters = max(i["iters"] for i in infos[-nr:])
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -696,6 +714,22 @@ def run_ours(args, rank, world, local):
         out["w4_uneven_batch16"] = run_batch(args, rank, world, local, steps=5, sub=True)
         out["dd_32x32x32x64_f32"] = measure_dd(wl, local)
     return out
+
+
+def run_dd(args, rank, world, local):
+    """The decomposed operator alone (one process holds every block)."""
+    import dataclasses
+
+    import torch
+    from paper_1811_00893_gb300.workloads import by_index
+
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local)
+    wl = by_index(args.workload)
+    if args.dims:
+        wl = dataclasses.replace(wl, dims=tuple(int(v) for v in args.dims.split(",")))
+    return {"impl": "ours", "decomposition": measure_dd(wl, local, launches=max(1, args.steps), repeats=1)}
 
 
 # ---------------------------------------------------------------------------
@@ -913,6 +947,8 @@ def main(argv=None):
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world, local)
+    elif args.dd:
+        out = run_dd(args, rank, world, local)
     elif args.workload == BATCH_INDEX:
         out = run_batch(args, rank, world, local)
     else:

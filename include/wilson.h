@@ -219,8 +219,9 @@ typedef struct {
                           instead of restarted defect correction */
     int use_x0;        /* 1: x holds the initial guess */
     int graph_iters;   /* > 0: capture this many iterations per CUDA-graph replay (the host
-                          checks convergence after each replay); <= 0: eager launches with
-                          a host check every max(1, -graph_iters) iterations (4 when 0) */
+                          checks convergence after each replay); 0: the same with 4; < 0:
+                          eager launches with a host check every -graph_iters iterations.
+                          A chunk the solver predicts shorter than this runs eagerly. */
 } wl_solve_params;
 
 typedef struct {
@@ -395,7 +396,7 @@ int wl_cdot_dd(wl_dd dd, double* out, const void* const* a, const void* const* b
  * decomposed M_ee (two halo exchanges) and sums its dot products over the
  * blocks (one allreduce per reduction).  x[k], b[k]: block-local canonical
  * FP64 fields (device), nrhs each.  Even-odd systems only (p->eo = 1), eager
- * launches (graph_iters is read as the host-check interval).  info has nrhs
+ * launches (|graph_iters| is read as the host-check interval, 4 when 0).  info has nrhs
  * entries.  Synchronises the stream. */
 int wilson_solve_dd(wl_dd dd, double* const* x, const double* const* b, int nrhs, const wl_solve_params* p,
                     wl_solve_info* info, void* stream);
@@ -424,8 +425,11 @@ long long wl_launch_count(void);
 double wl_algorithmic_bytes(void);
 
 /* Per-launch CUDA-event timing of the hopping kernels launched by this gauge
- * object (eager launches only; launches inside graph capture are not timed):
- * enable = 1 clears and starts recording, enable = 0 stops.  wl_timing_read
+ * object: eager launches, and the launches of wilson_solve's graph replays
+ * (each replay adds one record per hopping launch of the graph, read from
+ * event-record nodes once the replay has run); launches in other captured
+ * graphs are not timed.  enable = 1 clears and starts recording, enable = 0
+ * stops.  wl_timing_read
  * returns, for hopping launches of precision `prec` (-1: all), the summed
  * kernel time in ms, the number of timed launches and their summed
  * algorithmic bytes, leaving out launches that found no work (a solver

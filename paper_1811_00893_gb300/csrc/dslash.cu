@@ -86,6 +86,13 @@ static const int kPipeShape = 16;
 // Single-RHS reducing launches: block size (grid of resident blocks), or
 // kFullGrid + block size (full grid and a finishing launch).
 static const int kFullGrid = 1000;
+// Single-RHS FP64 Wilson launches: three threads per site (hop_rows_kernel).
+static const int kRowsShape = 2000;
+
+static bool rows_allowed(const HopLaunch& h, int lf)
+{
+    return h.prec == WL_F64 && h.cl_mode == kClNone && lf == 0;
+}
 
 // Resident-block grid of the reducing single-RHS hop kernel.
 static int single_grid_cap(const HopLaunch& h, int lf, int block)
@@ -106,7 +113,15 @@ static int launch_shape(const HopLaunch& h, int lf, HopArgs& A, int nrhs, int sh
     A.blocks_per_parity = (int)bpp;
     A.nparity = h.nparity;
     unsigned gx = (unsigned)(bpp * h.nparity);
-    if (!multi) {
+    if (!multi && shape == kRowsShape) {
+        A.blocks_per_parity = (int)((A.g.Vh + kRowSites - 1) / kRowSites);
+        A.partials_only = h.dot ? 1 : 0;
+        gx = (unsigned)((long long)A.blocks_per_parity * h.nparity);
+        HopKernels<kClNone, 0>::rows(h.dagger != 0, h.dot, A, dim3(gx, 1), s);
+        if (h.dot)
+            return launch_finish_slots(A.red.partial, (long long)A.red.max_blocks * 3, (int)gx, 1, A.dot_out,
+                                       A.dot_stride, A.active, A.active_stride, s);
+    } else if (!multi) {
         // shapes above kFullGrid: the reducing kernel over the full grid, one
         // site per thread, with a finishing launch for the partial sums
         const bool full = shape > kFullGrid;
@@ -170,7 +185,8 @@ static int tuned_shape(wl_gauge g, const HopLaunch& h, int lf, HopArgs& A, int n
         const char* fb = getenv("WL_HOP_BLOCK");
         const int v = fb ? atoi(fb) : 0;
         const int b = v > kFullGrid ? v - kFullGrid : v;
-        if ((b == 64 || b == 128 || b == 256) && (v < kFullGrid || h.dot)) {
+        if (((b == 64 || b == 128 || b == 256) && (v < kFullGrid || h.dot)) ||
+            (v == kRowsShape && rows_allowed(h, lf))) {
             *shape = v;
             return WL_OK;
         }
@@ -196,6 +212,7 @@ static int tuned_shape(wl_gauge g, const HopLaunch& h, int lf, HopArgs& A, int n
         cand = {64, 128, 256};
         if (h.dot)
             for (int b : {64, 128, 256}) cand.push_back(kFullGrid + b);
+        if (rows_allowed(h, lf)) cand.push_back(kRowsShape);
     }
     cudaEvent_t e0, e1;
     WL_CUDA(cudaEventCreate(&e0));

@@ -323,25 +323,93 @@ int ensure_tmp(wl_gauge g, int prec, size_t bytes)
 // ---------------------------------------------------------------------------
 
 static const size_t kTimingPool = 1 << 14;
+static const size_t kCapturePool = 256;  // timed launches in one solver graph
 
 void timing_begin(wl_gauge g, cudaStream_t s, double bytes, int prec, int* slot)
 {
     *slot = -1;
     Timing& t = g->timing;
     if (!t.on) return;
-    if (is_capturing(s) || t.used >= t.start.size()) {
+    if (is_capturing(s)) {  // a capture slot (slot = -2 - index), or dropped outside solver graphs
+        if (!t.capturing || t.cused >= t.cstart.size()) {
+            t.dropped++;
+            return;
+        }
+        const size_t c = t.cused++;
+        t.cbytes[c] = bytes;
+        t.cprec[c] = prec;
+        *slot = -2 - (int)c;
+        // an event-record node of the graph (a plain record would only mark a
+        // dependency inside the capture)
+        cudaEventRecordWithFlags(t.cstart[c], s, cudaEventRecordExternal);
+        return;
+    }
+    if (t.used >= t.start.size()) {
         t.dropped++;
         return;
     }
     *slot = (int)t.used++;
     t.bytes[*slot] = bytes;
     t.prec[*slot] = prec;
+    t.fixed[*slot] = -1.f;
     cudaEventRecord(t.start[*slot], s);
 }
 
 void timing_end(wl_gauge g, cudaStream_t s, int slot)
 {
     if (slot >= 0) cudaEventRecord(g->timing.stop[slot], s);
+    else if (slot <= -2) cudaEventRecordWithFlags(g->timing.cstop[-2 - slot], s, cudaEventRecordExternal);
+}
+
+void timing_capture_begin(wl_gauge g)
+{
+    Timing& t = g->timing;
+    timing_harvest(g);  // the capture slots are about to be recorded by another graph
+    t.cused = 0;
+    t.capturing = t.on;
+}
+
+size_t timing_capture_end(wl_gauge g)
+{
+    Timing& t = g->timing;
+    const size_t n = t.capturing ? t.cused : 0;
+    t.capturing = false;
+    return n;
+}
+
+void timing_replayed(wl_gauge g, size_t nslots)
+{
+    Timing& t = g->timing;
+    if (!t.on) return;
+    for (size_t c = 0; c < nslots; ++c) {
+        if (t.used >= t.start.size()) {
+            t.dropped++;
+            continue;
+        }
+        const size_t q = t.used++;
+        t.bytes[q] = t.cbytes[c];
+        t.prec[q] = t.cprec[c];
+        t.fixed[q] = -1.f;
+        t.pending.push_back({q, c});
+    }
+}
+
+int timing_harvest(wl_gauge g)
+{
+    Timing& t = g->timing;
+    for (const auto& pc : t.pending) {
+        float e = 0.f;
+        if (cudaEventSynchronize(t.cstop[pc.second]) != cudaSuccess ||
+            cudaEventElapsedTime(&e, t.cstart[pc.second], t.cstop[pc.second]) != cudaSuccess) {
+            cudaGetLastError();  // timing is a diagnostic: leave the record out, not the solve
+            t.bytes[pc.first] = -1.0;
+            t.dropped++;
+            continue;
+        }
+        t.fixed[pc.first] = e;
+    }
+    t.pending.clear();
+    return WL_OK;
 }
 
 }  // namespace wl
@@ -505,6 +573,8 @@ extern "C" int wl_gauge_destroy(wl_gauge g)
     if (g->red.ticket) cudaFree(g->red.ticket);
     for (auto e : g->timing.start) cudaEventDestroy(e);
     for (auto e : g->timing.stop) cudaEventDestroy(e);
+    for (auto e : g->timing.cstart) cudaEventDestroy(e);
+    for (auto e : g->timing.cstop) cudaEventDestroy(e);
     delete g;
     return WL_OK;
 }
@@ -599,11 +669,21 @@ extern "C" int wl_timing(wl_gauge g, int enable)
             t.stop.resize(kTimingPool);
             t.bytes.resize(kTimingPool);
             t.prec.resize(kTimingPool);
+            t.fixed.resize(kTimingPool);
             for (size_t k = 0; k < kTimingPool; ++k) {
                 WL_CUDA(cudaEventCreate(&t.start[k]));
                 WL_CUDA(cudaEventCreate(&t.stop[k]));
             }
+            t.cstart.resize(kCapturePool);
+            t.cstop.resize(kCapturePool);
+            t.cbytes.resize(kCapturePool);
+            t.cprec.resize(kCapturePool);
+            for (size_t k = 0; k < kCapturePool; ++k) {
+                WL_CUDA(cudaEventCreate(&t.cstart[k]));
+                WL_CUDA(cudaEventCreate(&t.cstop[k]));
+            }
         }
+        t.pending.clear();
         t.used = 0;
         t.dropped = 0;
     }
@@ -615,15 +695,18 @@ extern "C" int wl_timing_read(wl_gauge g, int prec, double* ms, long long* launc
 {
     if (!g) return set_error(WL_ERR_ARG, "NULL gauge object");
     Timing& t = g->timing;
+    WL_TRY(timing_harvest(g));
     double total = 0.0, b = 0.0;
     long long n = 0;
     for (size_t k = 0; k < t.used; ++k) {
         if (prec >= 0 && t.prec[k] != prec) continue;
         if (t.bytes[k] < 0.0) continue;  // a launch that found no work (solver chunk tail)
         ++n;
-        WL_CUDA(cudaEventSynchronize(t.stop[k]));
-        float e = 0.f;
-        WL_CUDA(cudaEventElapsedTime(&e, t.start[k], t.stop[k]));
+        float e = t.fixed[k];
+        if (e < 0.f) {
+            WL_CUDA(cudaEventSynchronize(t.stop[k]));
+            WL_CUDA(cudaEventElapsedTime(&e, t.start[k], t.stop[k]));
+        }
         total += e;
         b += t.bytes[k];
     }

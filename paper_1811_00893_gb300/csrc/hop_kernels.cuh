@@ -262,6 +262,102 @@ __global__ void __launch_bounds__(256, 2) hop_mrhs_pipe_kernel(const HopArgs A, 
     }
 }
 
+// FP64 hopping term for small lattices, where one thread per site leaves
+// most SMs with less than a warp and the kernel's time is the latency of one
+// thread's dependent FP64 chain: three threads per output site, one colour
+// row a each (output components 3 s + a).  Each projects the full neighbour
+// spinors (the three rows read them from L1) and applies row a of every link,
+// a third of hop_kernel's chain per thread and no exchange between the three.
+// Every output component sees hop_kernel's operations in the same order.
+// Block: kRowSites sites x 3 rows (thread t: row t / kRowSites); a reducing
+// launch leaves one partial per block for the finishing launch.
+static constexpr int kRowSites = 64;
+
+template <int D, int MU, int S>
+__device__ __forceinline__ void hop_row(cx<double> (&acc)[12], const char* in, long long Vh, int nb,
+                                        const void* links, int i, int a)
+{
+    cx<double> h0[3], h1[3], w[3];
+    load_project<WL_F64, MU, S>(h0, h1, in, Vh, nb);
+    load_link_row<WL_F64>(w, links, Vh, D, i, a);
+    reconstruct<MU, S>(acc, 0, dot3(w[0], w[1], w[2], h0), dot3(w[0], w[1], w[2], h1));
+}
+
+template <bool DAG, bool DOT>
+__global__ void __launch_bounds__(3 * kRowSites) hop_rows_kernel(const HopArgs A)
+{
+    const int rhs = blockIdx.y;
+    if (A.active && A.active[rhs * A.active_stride] == 0) return;  // uniform per block
+    const int pidx = blockIdx.x / A.blocks_per_parity;
+    const int a = threadIdx.x / kRowSites;
+    const int i = (blockIdx.x - pidx * A.blocks_per_parity) * kRowSites + (threadIdx.x - a * kRowSites);
+    const long long Vh = A.g.Vh;
+    double part[3] = {0, 0, 0};
+    if (i < Vh) {
+        int nb[8];
+        neighbours(A.g, A.parity0 + pidx, i, nb);
+        const char* in = A.in[pidx] + rhs * A.rs_in;
+        const void* links = A.links[pidx];
+        cx<double> acc[12];  // the rows of colour a at 0, 3, 6, 9
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = {0.0, 0.0};
+        constexpr int F = DAG ? +1 : -1;  // forward projector sign
+        constexpr int B = -F;
+        hop_row<0, 0, F>(acc, in, Vh, nb[0], links, i, a);
+        hop_row<1, 0, B>(acc, in, Vh, nb[1], links, i, a);
+        hop_row<2, 1, F>(acc, in, Vh, nb[2], links, i, a);
+        hop_row<3, 1, B>(acc, in, Vh, nb[3], links, i, a);
+        hop_row<4, 2, F>(acc, in, Vh, nb[4], links, i, a);
+        hop_row<5, 2, B>(acc, in, Vh, nb[5], links, i, a);
+        hop_row<6, 3, F>(acc, in, Vh, nb[6], links, i, a);
+        hop_row<7, 3, B>(acc, in, Vh, nb[7], links, i, a);
+        // epilogue (as epilogue_ptrs, on this thread's four components)
+        auto at = [&](const char* q, long long rs) -> const double2* {
+            return q ? (const double2*)(q + rhs * rs) : nullptr;
+        };
+        const double2* x1 = at(A.x1[pidx], A.rs_x1);
+        const double2* x2 = at(A.x2[pidx], A.rs_x2);
+        const double2* w = at(A.w[pidx], A.rs_w);
+        double2* out = (double2*)(A.out[pidx] + rhs * A.rs_out);
+        const double sa = A.a, b1 = A.b1;
+        cx<double> v[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) v[s] = sa * acc[3 * s];
+        if (x1)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const double2 t = x1[(3 * s + a) * Vh + i];
+                v[s] = v[s] + cx<double>{t.x, t.y};
+            }
+        if (x2)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const double2 t = x2[(3 * s + a) * Vh + i];
+                v[s] = v[s] + b1 * cx<double>{t.x, t.y};
+            }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) out[(3 * s + a) * Vh + i] = make_double2(v[s].re, v[s].im);
+        if (DOT) {
+            if (w)
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    const double2 t = w[(3 * s + a) * Vh + i];
+                    part[0] = fma(t.x, v[s].re, fma(t.y, v[s].im, part[0]));
+                    part[1] = fma(t.x, v[s].im, fma(-t.y, v[s].re, part[1]));
+                }
+#pragma unroll
+            for (int s = 0; s < 4; ++s) part[2] = fma(v[s].re, v[s].re, fma(v[s].im, v[s].im, part[2]));
+        }
+    }
+    if constexpr (DOT) {
+        warp_sum<3>(part);
+        __shared__ double sh[3 * 32];
+        block_sum_warps<3>(part, sh);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 3; ++k) A.red.partial[((long long)rhs * A.red.max_blocks + blockIdx.x) * 3 + k] = part[k];
+    }
+}
+
 // Host-side launchers of one clover mode and link format (LF = 1 exists for
 // FP32 and FP16 only; other precisions are never requested with it).
 template <int CL, int LF = 0>
@@ -274,6 +370,8 @@ struct HopKernels {
     static void pipe(int prec, bool dagger, bool dot, const HopArgs& A, int nrhs, int ntiles, dim3 grid,
                      dim3 block, size_t smem, cudaStream_t s);
     static const void* pipe_kernel(int prec, bool dagger, bool dot);
+    // three threads per site (FP64, CL = 0, LF = 0 only), kRowSites sites per block
+    static void rows(bool dagger, bool dot, const HopArgs& A, dim3 grid, cudaStream_t s);
     // the reducing single-RHS kernel (for occupancy queries)
     static const void* reducing(int prec, bool dagger);
 };
@@ -361,6 +459,21 @@ void HopKernels<CL, LF>::multi(int prec, bool dagger, bool dot, const HopArgs& A
     else if constexpr (LF == 0) {
         if (prec == WL_F64) hop_multi_p<CL, LF, WL_F64>(dagger, dot, A, nrhs, grid, block, smem, s);
         else hop_multi_p<CL, LF, WL_DF64>(dagger, dot, A, nrhs, grid, block, smem, s);
+    }
+}
+
+template <int CL, int LF>
+void HopKernels<CL, LF>::rows(bool dagger, bool dot, const HopArgs& A, dim3 grid, cudaStream_t s)
+{
+    if constexpr (CL == kClNone && LF == 0) {
+        const int block = 3 * kRowSites;
+        if (dagger) {
+            if (dot) hop_rows_kernel<true, true><<<grid, block, 0, s>>>(A);
+            else hop_rows_kernel<true, false><<<grid, block, 0, s>>>(A);
+        } else {
+            if (dot) hop_rows_kernel<false, true><<<grid, block, 0, s>>>(A);
+            else hop_rows_kernel<false, false><<<grid, block, 0, s>>>(A);
+        }
     }
 }
 

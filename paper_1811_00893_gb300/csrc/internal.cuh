@@ -29,8 +29,17 @@ struct Timing {
     std::vector<cudaEvent_t> start, stop;
     std::vector<double> bytes;
     std::vector<int> prec;
+    std::vector<float> fixed;  // ms of a slot read from a graph replay; < 0: read the slot's events
     size_t used = 0;
     long long dropped = 0;
+    // Launches inside a captured solver graph ("capture slots"): their event
+    // records are graph nodes, recorded again by every replay.
+    std::vector<cudaEvent_t> cstart, cstop;
+    std::vector<double> cbytes;
+    std::vector<int> cprec;
+    size_t cused = 0;
+    bool capturing = false;
+    std::vector<std::pair<size_t, size_t>> pending;  // (slot, capture slot) of the last replay
 };
 
 struct Workspace;  // solver.cu
@@ -137,6 +146,14 @@ int launch_hop(wl_gauge g, const HopLaunch& h, cudaStream_t s);
 // record-or-not helpers for per-launch timing
 void timing_begin(wl_gauge g, cudaStream_t s, double bytes, int prec, int* slot);
 void timing_end(wl_gauge g, cudaStream_t s, int slot);
+// Solver graphs: launches captured between timing_capture_begin and
+// timing_capture_end are timed by capture slots; after each replay,
+// timing_replayed appends one record per capture slot, and timing_harvest
+// reads the replay's times (before the next replay records them again).
+void timing_capture_begin(wl_gauge g);
+size_t timing_capture_end(wl_gauge g);
+void timing_replayed(wl_gauge g, size_t nslots);
+int timing_harvest(wl_gauge g);
 
 // BLAS-1 / reductions (blas.cu).  Vectors are `nhalf` half fields per rhs
 // back to back; rhs stride = nhalf * spinor_field_bytes(prec, Vh).

@@ -433,7 +433,7 @@ void discount_chunk(wl_gauge g, Workspace* w, int skipped)
     if (skipped <= 0 || w->chunk_k <= 0) return;
     if (skipped > w->chunk_k) skipped = w->chunk_k;
     g_bytes.fetch_sub(w->chunk_bytes / w->chunk_k * skipped);
-    const size_t slots = w->chunk_slot1 - w->chunk_slot0;  // eager launches only
+    const size_t slots = w->chunk_slot1 - w->chunk_slot0;  // this chunk's timed launches
     if (slots % (size_t)w->chunk_k == 0) {
         const size_t per_iter = slots / (size_t)w->chunk_k;
         for (size_t q = w->chunk_slot1 - per_iter * skipped; q < w->chunk_slot1; ++q)
@@ -448,18 +448,22 @@ static int run_chunk_impl(wl_gauge g, Workspace* w, int nrhs, int k, bool use_gr
         for (int it = 0; it < k; ++it) WL_TRY(enqueue_iteration(g, w, nrhs, s));
         return WL_OK;
     }
-    if (!w->graph || w->graph_k != k || w->graph_nrhs != nrhs || w->graph_red_gen != g->red_gen) {
+    const bool timed = g->timing.on;
+    if (!w->graph || w->graph_k != k || w->graph_nrhs != nrhs || w->graph_red_gen != g->red_gen ||
+        w->graph_timed != timed) {
         if (w->graph) cudaGraphExecDestroy(w->graph);
         w->graph = nullptr;
         // capture on a private stream (the legacy default stream cannot be
         // captured); the graph is then launched on the caller's stream
         if (!w->cap_stream) WL_CUDA(cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking));
         const long long c0 = g_launches.load(), b0 = g_bytes.load();
+        timing_capture_begin(g);
         WL_CUDA(cudaStreamBeginCapture(w->cap_stream, cudaStreamCaptureModeThreadLocal));
         int rc = WL_OK;
         for (int it = 0; it < k && rc == WL_OK; ++it) rc = enqueue_iteration(g, w, nrhs, w->cap_stream);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(w->cap_stream, &graph);
+        w->graph_tslots = timing_capture_end(g);
         if (rc != WL_OK) {
             if (graph) cudaGraphDestroy(graph);
             return rc;
@@ -475,9 +479,12 @@ static int run_chunk_impl(wl_gauge g, Workspace* w, int nrhs, int k, bool use_gr
         w->graph_k = k;
         w->graph_nrhs = nrhs;
         w->graph_red_gen = g->red_gen;
+        w->graph_timed = timed;
     }
+    WL_TRY(timing_harvest(g));  // the previous replay's times, before this one records them again
     WL_CUDA(cudaGraphLaunch(w->graph, s));
     count_launch(w->graph_kernels, (double)w->graph_bytes);
+    if (w->graph_timed) timing_replayed(g, w->graph_tslots);
     return WL_OK;
 }
 
@@ -813,8 +820,9 @@ int SolveState::begin(wl_gauge g_, double* x, const double* b, int nrhs_, const 
     // default inner reduction per round: FP32 to 3e-6 (a sweep over 1e-4 .. 3e-7
     // on the 32^3 x 64, 12-RHS and clover workloads found it fastest), FP16 to 1e-3
     inner_tol = prm->inner_tol > 0.0 ? prm->inner_tol : (P == WL_F64 ? 0.0 : P == WL_F32 ? 3e-6 : 1e-3);
+    // iterations per host check; replayed as a CUDA graph unless graph_iters < 0
     chunk = prm->graph_iters > 0 ? prm->graph_iters : prm->graph_iters < 0 ? -prm->graph_iters : 4;
-    use_graph = prm->graph_iters > 0;
+    use_graph = prm->graph_iters >= 0;
     safety = 0.5;  // aim below tol on the Schur residual; tightened if the true residual misses
     final_rounds = 0;
     return WL_OK;

@@ -70,6 +70,8 @@ struct Workspace {
     int graph_red_gen = -1;
     long long graph_kernels = 0;
     long long graph_bytes = 0;
+    bool graph_timed = false;   // captured while per-launch timing was on
+    size_t graph_tslots = 0;    // its timed launches (capture slots)
     cudaStream_t cap_stream = nullptr;  // private stream for graph capture
 };
 

@@ -281,6 +281,79 @@ def test_reducing_hop_shapes_in_solve(monkeypatch, shape):
 
 
 # ----------------------------------------------------------------------------
+# FP64 on small lattices: three threads per site (launch shape 2000)
+# ----------------------------------------------------------------------------
+
+def _fp64_ops(monkeypatch, shape, dims, bc):
+    """Hopping term (both parities and signs), D and M_ee (both signs) in FP64
+    on a fresh gauge object whose hopping launches take `shape`."""
+    monkeypatch.setenv("WL_HOP_BLOCK", str(shape))
+    c = Case(dims, kappa=0.124, kind="haar", seed=41, bc=bc)
+    try:
+        psi = c.source(nrhs=1, seed=43)
+        outs = []
+        for dagger in (0, 1):
+            for p in (0, 1):
+                inp = c.to_internal(psi, 1 - p, "f64")
+                out = c.g.field("f64", 1)
+                wilson.wilson_dslash(c.g.handle, out, inp, p, dagger, wilson.WL_F64, 1)
+                outs.append(("dslash", p, dagger, out.clone()))
+            inp = full_internal(c, psi, "f64")
+            out = torch.empty_like(inp)
+            wilson.wilson_mult(c.g.handle, out, inp, 0, dagger, wilson.WL_F64, 1)
+            outs.append(("D", 0, dagger, out.clone()))
+            inp = c.to_internal(psi, 0, "f64")
+            out = c.g.field("f64", 1)
+            wilson.wilson_mult(c.g.handle, out, inp, 1, dagger, wilson.WL_F64, 1)
+            outs.append(("Mee", 0, dagger, out.clone()))
+        torch.cuda.synchronize()
+        return c, psi, outs
+    except Exception:
+        c.close()
+        raise
+
+
+@pytest.mark.parametrize("dims", [(6, 4, 4, 6), (4, 4, 4, 4)])  # Vh = 288 (ragged), 128
+def test_fp64_rows_kernel_equals_one_thread_per_site(monkeypatch, dims):
+    """The three-threads-per-site FP64 hop gives the one-thread-per-site
+    kernel's result bit for bit (same operations per output component), and
+    both match the oracle."""
+    bc = (1, 1, 1, -1)
+    c1, psi, ref = _fp64_ops(monkeypatch, 128, dims, bc)
+    c1.close()
+    c2, _, got = _fp64_ops(monkeypatch, 2000, dims, bc)
+    try:
+        for (name, p, dagger, a), (_, _, _, b) in zip(ref, got):
+            assert torch.equal(a, b), (name, p, dagger)
+        # and the oracle, for the hopping term of each parity
+        for name, p, dagger, out in got:
+            if name != "dslash":
+                continue
+            have = c2.half(c2.to_canonical(out, p, "f64"), p)
+            want = oracle.hop_eo(c2.U, c2.half(psi, 1 - p), dims, bc, p, dagger=bool(dagger))
+            assert rel(have, want) < TOL["f64"], (p, dagger)
+    finally:
+        c2.close()
+
+
+def test_fp64_rows_kernel_in_solves(monkeypatch):
+    """The reducing form of the three-threads-per-site hop drives the FP64
+    full-D and even-odd solves to the oracle's true residual."""
+    monkeypatch.setenv("WL_HOP_BLOCK", "2000")
+    c = Case((6, 4, 4, 6), kappa=0.124, kind="haar", seed=47, bc=(1, 1, 1, -1))
+    try:
+        b = c.source(nrhs=1, seed=48)
+        for eo in (False, True):
+            x = torch.zeros_like(b)
+            rc, info = wilson.wilson_solve(c.g.handle, x, b, 1,
+                                           wilson.solve_params(tol=1e-10, eo=eo, inner=wilson.WL_F64))
+            tr = oracle.true_residual(c.U, b[0].cpu().numpy(), x[0].cpu().numpy(), c.dims, c.bc, c.kappa)
+            assert tr <= 1e-10 and abs(info[0]["true_resid"] - tr) <= 0.05 * tr + 1e-15, eo
+    finally:
+        c.close()
+
+
+# ----------------------------------------------------------------------------
 # FP16 error margins: the measured relative errors of every FP16 operator on
 # every parity lattice, printed (pytest -s) and held against TOL["f16"]
 # ----------------------------------------------------------------------------

@@ -81,6 +81,32 @@ def test_multi_rhs_and_graphs(graph_iters):
         c.close()
 
 
+def test_timing_sees_graph_replays():
+    """The per-launch timing records the hopping launches of the solver's graph
+    replays like eager ones, and replaying the iterations changes no bit."""
+    c = Case((8, 8, 8, 16), kappa=0.124, kind="haar", seed=5)
+    try:
+        b = c.source(nrhs=1, seed=50)
+        got = {}
+        for gi in (-4, 4):
+            x = torch.zeros_like(b)
+            p = wilson.solve_params(tol=TOL, eo=True, inner=wilson.WL_F32, graph_iters=gi)
+            wilson.wilson_solve(c.g.handle, x, b, 1, p)  # capture outside the timed solve
+            x = torch.zeros_like(b)
+            wilson.wl_timing(c.g.handle, True)
+            rc, infos = wilson.wilson_solve(c.g.handle, x, b, 1, p)
+            wilson.wl_timing(c.g.handle, False)
+            check_solution(c, b, x, infos)
+            got[gi] = (x, infos[0]["iters"], wilson.wl_timing_read(c.g.handle, wilson.WL_F32))
+        (xe, ie, (mse, ne, be)), (xg, ig, (msg, ng, bg)) = got[-4], got[4]
+        assert ig == ie and torch.equal(xg, xe)
+        assert ne == ng and be == bg
+        assert abs(ne - 4 * ie) <= 4  # two hops per M_ee, two M_ee per iteration
+        assert mse > 0 and msg > 0 and 0.2 < msg / mse < 5
+    finally:
+        c.close()
+
+
 def test_resume_from_initial_guess(c8):
     b = c8.source(nrhs=1, seed=2002)
     x = torch.zeros_like(b)
