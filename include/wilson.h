@@ -286,10 +286,10 @@ int wilson_solve_batch(int nlat, const wl_gauge* gs, double* const* x, const dou
  *
  * All blocks live on the calling thread's current GPU.  The calls are
  * asynchronous on `stream` except wl_dd_create, wl_dd_destroy,
- * wl_dd_set_exchange and wilson_solve_dd.  Block gauge objects belong to the
- * decomposition: wilson_dslash, wilson_mult, wilson_solve(_batch) and
- * wl_clover_set refuse them (WL_ERR_STATE); there is no clover term in the
- * decomposed operator.
+ * wl_dd_set_exchange, wl_dd_clover_set and wilson_solve_dd.  Block gauge
+ * objects belong to the decomposition: wilson_dslash, wilson_mult,
+ * wilson_solve(_batch) and wl_clover_set refuse them (WL_ERR_STATE); the
+ * clover term of the decomposed operator is attached with wl_dd_clover_set.
  * ---------------------------------------------------------------------- */
 typedef struct wl_dd_s* wl_dd;
 
@@ -372,6 +372,15 @@ int wl_dd_block(wl_dd dd, int k, wl_gauge* g, int coord[4]);
  * neighbours' halos.  Both run on a second stream, overlapping the interior
  * sweep.  Synchronises the device. */
 int wl_dd_set_exchange(wl_dd dd, int mode);
+
+/* Clover term of the decomposed operator (Eq. 2): F as for wl_clover_set,
+ * for the whole lattice (device, canonical order, read during the call); each
+ * block held here takes its sites' matrices.  From then on wilson_mult_dd and
+ * wilson_solve_dd use D_clov (the fused clover epilogues of the undivided
+ * operator, so the result is again bit for bit the undivided one);
+ * wilson_dslash_dd stays the hopping term.  F = NULL detaches the term.  Errors
+ * as wl_clover_set; on error no block keeps a term.  Synchronises the stream. */
+int wl_dd_clover_set(wl_dd dd, const double* F, void* stream);
 
 /* Copy nrhs canonical FP64 fields of the whole lattice (`global`, device,
  * nrhs*V*12 complex) to block-local canonical fields of the held blocks

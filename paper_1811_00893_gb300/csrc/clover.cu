@@ -253,12 +253,11 @@ int launch_clover_apply(wl_gauge g, int prec, void* out, const void* in, int par
 
 using namespace wl;
 
-extern "C" int wl_clover_set(wl_gauge g, const double* F, void* stream)
+namespace wl {
+
+// wl_clover_set without the entry checks (also attaches a block's term)
+int clover_set(wl_gauge g, const double* F, cudaStream_t s)
 {
-    WL_ENTRY();
-    if (!g) return set_error(WL_ERR_ARG, "NULL gauge object");
-    if (g->dd_part) return set_error(WL_ERR_STATE, "block of a domain decomposition: use the _dd calls");
-    cudaStream_t s = (cudaStream_t)stream;
     if (!F) {
         WL_CUDA(cudaStreamSynchronize(s));
         free_clover(g);
@@ -327,6 +326,16 @@ extern "C" int wl_clover_set(wl_gauge g, const double* F, void* stream)
     }
     g->has_clover = true;
     return WL_OK;
+}
+
+}  // namespace wl
+
+extern "C" int wl_clover_set(wl_gauge g, const double* F, void* stream)
+{
+    WL_ENTRY();
+    if (!g) return set_error(WL_ERR_ARG, "NULL gauge object");
+    if (g->dd_part) return set_error(WL_ERR_STATE, "block of a domain decomposition: use the _dd calls");
+    return clover_set(g, F, (cudaStream_t)stream);
 }
 
 extern "C" int wl_clover_apply(wl_gauge g, void* out, const void* in, int parity, int inverse,

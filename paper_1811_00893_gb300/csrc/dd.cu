@@ -14,8 +14,27 @@
 
 namespace wl {
 
-extern template struct DDKernels<0>;  // dd_hop.cu
-extern template struct DDKernels<1>;  // dd_hop_r12.cu
+extern template struct DDKernels<0, kClNone>;  // dd_hop.cu
+extern template struct DDKernels<1, kClNone>;  // dd_hop_r12.cu
+extern template struct DDKernels<0, kClX2>;    // dd_hop_clover.cu
+extern template struct DDKernels<0, kClOut>;
+extern template struct DDKernels<1, kClX2>;    // dd_hop_r12_clover.cu
+extern template struct DDKernels<1, kClOut>;
+
+// the kernel family of a launch: link format and clover mode
+static void dd_hop_family(int lf, int cl, int prec, bool dagger, bool dot, bool bnd, const DDArgs& A, dim3 grid,
+                          cudaStream_t s)
+{
+    if (lf) {
+        if (cl == kClX2) DDKernels<1, kClX2>::hop(prec, dagger, dot, bnd, A, grid, s);
+        else if (cl == kClOut) DDKernels<1, kClOut>::hop(prec, dagger, dot, bnd, A, grid, s);
+        else DDKernels<1, kClNone>::hop(prec, dagger, dot, bnd, A, grid, s);
+    } else {
+        if (cl == kClX2) DDKernels<0, kClX2>::hop(prec, dagger, dot, bnd, A, grid, s);
+        else if (cl == kClOut) DDKernels<0, kClOut>::hop(prec, dagger, dot, bnd, A, grid, s);
+        else DDKernels<0, kClNone>::hop(prec, dagger, dot, bnd, A, grid, s);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // canonical global field <-> block-local canonical fields
@@ -25,9 +44,10 @@ struct Origin {
     int o[4];
 };
 
-// dir = 0: local <- global; dir = 1: global <- local
+// dir = 0: local <- global; dir = 1: global <- local; nd doubles per site
+// (24: a spinor, 144: a clover matrix)
 __global__ void dd_copy_canonical_kernel(double* loc, double* glob, Geom gl, Geom gg, Origin org,
-                                         long long Vl, long long Vg, int dir)
+                                         long long Vl, long long Vg, int dir, int nd)
 {
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int rhs = blockIdx.y;
@@ -39,12 +59,12 @@ __global__ void dd_copy_canonical_kernel(double* loc, double* glob, Geom gl, Geo
         r /= gl.L[mu];
     }
     const long long sg = c[0] + (long long)gg.L[0] * (c[1] + (long long)gg.L[1] * (c[2] + (long long)gg.L[2] * c[3]));
-    double2* pl = (double2*)(loc + ((long long)rhs * Vl + s) * 24);
-    double2* pg = (double2*)(glob + ((long long)rhs * Vg + sg) * 24);
+    double2* pl = (double2*)(loc + ((long long)rhs * Vl + s) * nd);
+    double2* pg = (double2*)(glob + ((long long)rhs * Vg + sg) * nd);
     if (dir == 0)
-        for (int k = 0; k < 12; ++k) pl[k] = pg[k];
+        for (int k = 0; k < nd / 2; ++k) pl[k] = pg[k];
     else
-        for (int k = 0; k < 12; ++k) pg[k] = pl[k];
+        for (int k = 0; k < nd / 2; ++k) pg[k] = pl[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -327,6 +347,10 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
             D.x1[k] = (const char*)h.x1[d][k];
             D.x2[k] = (const char*)h.x2[d][k];
             D.w[k] = (const char*)h.w[d][k];
+            // clover epilogue: A (kClX2, on x2) or A^-1 (kClOut) of the output parity
+            D.cl[k] = h.cl_mode ? gd->clov[P][p][h.cl_mode == kClOut ? 1 : 0] : nullptr;
+            if (h.cl_mode && !D.cl[k])
+                return set_error(WL_ERR_STATE, "decomposition has no clover term in the requested precision");
         }
         D.halo = dd->recv[d];
         D.active = h.active[d];
@@ -343,7 +367,7 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
     }
     const int extra = (h.x1[0][0] ? 1 : 0) + (h.x2[0][0] ? 1 : 0) + (h.w[0][0] ? 1 : 0);
     const double site_bytes = (double)(lf ? (P == WL_F32 ? 384 : 192) : link_field_bytes(P, 1)) +
-                              (double)nrhs * (2 + extra) * sb;
+                              (h.cl_mode ? (double)clover_site_bytes(P) : 0.0) + (double)nrhs * (2 + extra) * sb;
     // part 0: interior (one contiguous range when only t is cut), part 1: boundary
     auto run = [&](int part, DDArgs AA, cudaStream_t st_) -> int {
         const long long n = part ? dd->nbnd : dd->nint;
@@ -354,8 +378,7 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
         AA.blocks_per_parity = part ? bb : bi;
         AA.block0 = part ? np * bi : 0;
         const dim3 grid((unsigned)(AA.blocks_per_parity * np), (unsigned)nrhs, (unsigned)dd->ndom);
-        if (lf) DDKernels<1>::hop(P, h.dagger != 0, h.dot, part == 1, AA, grid, st_);
-        else DDKernels<0>::hop(P, h.dagger != 0, h.dot, part == 1, AA, grid, st_);
+        dd_hop_family(lf, h.cl_mode, P, h.dagger != 0, h.dot, part == 1, AA, grid, st_);
         WL_CHECK_LAUNCH((double)dd->ndom * np * n * site_bytes);
         return WL_OK;
     };
@@ -384,7 +407,7 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
                 }
         }
         const dim3 grid((unsigned)((total + kDDBlock - 1) / kDDBlock), (unsigned)nrhs, (unsigned)dd->ndom);
-        DDKernels<0>::pack(P, h.dagger != 0, PA, grid, dd->comm);
+        dd_pack(P, h.dagger != 0, PA, grid, dd->comm);
         WL_CHECK_LAUNCH((double)nrhs * dd->ndom * total * (sb + 16 * halo_planes(P) + (P == WL_F16 ? 4 : 0)));
         // 2. exchange: device copies between held blocks, messages through the
         // transport for the rest
@@ -583,7 +606,15 @@ extern "C" int wl_dd_create_part(wl_dd* out, const wl_lattice* lat, const int* g
             rc = set_error(WL_ERR_CUDA, "site list upload");
             break;
         }
-        if (cudaStreamCreateWithFlags(&dd->comm, cudaStreamNonBlocking) != cudaSuccess ||
+        // the side stream (pack, exchange, boundary) at the highest priority:
+        // its blocks are scheduled ahead of the interior's waiting blocks, so
+        // the faces move early instead of after the interior sweep
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+            cudaGetLastError();
+            least = greatest = 0;
+        }
+        if (cudaStreamCreateWithPriority(&dd->comm, cudaStreamNonBlocking, greatest) != cudaSuccess ||
             cudaEventCreateWithFlags(&dd->ev_packed, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&dd->ev_exchanged, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
@@ -684,7 +715,7 @@ static int dd_canonical(wl_dd dd, double* const* loc, double* glob, int nrhs, in
         Origin org;
         for (int mu = 0; mu < 4; ++mu) org.o[mu] = dd->coord[d][mu] * dd->gloc.L[mu];
         const dim3 grid((unsigned)((Vl + 127) / 128), (unsigned)nrhs);
-        dd_copy_canonical_kernel<<<grid, 128, 0, s>>>(loc[d], glob, dd->gloc, dd->gglob, org, Vl, Vg, dir);
+        dd_copy_canonical_kernel<<<grid, 128, 0, s>>>(loc[d], glob, dd->gloc, dd->gglob, org, Vl, Vg, dir, 24);
         WL_CHECK_LAUNCH(2.0 * 192.0 * Vl * nrhs);
     }
     return WL_OK;
@@ -702,6 +733,39 @@ extern "C" int wl_dd_gather(wl_dd dd, double* global, const double* const* local
     return dd_canonical(dd, (double* const*)local, global, nrhs, 1, (cudaStream_t)stream);
 }
 
+extern "C" int wl_dd_clover_set(wl_dd dd, const double* F, void* stream)
+{
+    WL_ENTRY();
+    if (!dd) return set_error(WL_ERR_ARG, "NULL decomposition");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!F) {
+        for (int d = 0; d < dd->ndom; ++d) WL_TRY(clover_set(dd->dom[d], nullptr, s));
+        return WL_OK;
+    }
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, F) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return set_error(WL_ERR_ARG, "clover field must be device memory");
+    }
+    const long long Vl = 2 * dd->gloc.Vh, Vg = 2 * dd->gglob.Vh;
+    double* loc = nullptr;  // one block's F at a time
+    WL_CUDA(cudaMalloc((void**)&loc, sizeof(double) * 144 * Vl));
+    int rc = WL_OK;
+    for (int d = 0; d < dd->ndom && rc == WL_OK; ++d) {
+        Origin org;
+        for (int mu = 0; mu < 4; ++mu) org.o[mu] = dd->coord[d][mu] * dd->gloc.L[mu];
+        dd_copy_canonical_kernel<<<(unsigned)((Vl + 127) / 128), 128, 0, s>>>(loc, (double*)F, dd->gloc, dd->gglob,
+                                                                              org, Vl, Vg, 0, 144);
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(WL_ERR_CUDA, "clover scatter launch failed");
+        count_launch(1, 2.0 * 1152.0 * Vl);
+        if (rc == WL_OK) rc = clover_set(dd->dom[d], loc, s);  // synchronises the stream
+    }
+    cudaFree(loc);
+    if (rc != WL_OK)  // all blocks or none
+        for (int d = 0; d < dd->ndom; ++d) clover_set(dd->dom[d], nullptr, s);
+    return rc;
+}
+
 static int dd_check(wl_dd dd, const void* const* out, const void* const* in, wl_prec prec, int nrhs, int nhalf)
 {
     if (!dd) return set_error(WL_ERR_ARG, "NULL decomposition");
@@ -713,8 +777,6 @@ static int dd_check(wl_dd dd, const void* const* out, const void* const* in, wl_
         if (!out[d] || !in[d]) return set_error(WL_ERR_ARG, "NULL block field");
         if (!dd->dom[d]->links[prec][0])
             return set_error(WL_ERR_STATE, "decomposition was created without this precision");
-        if (dd->dom[d]->has_clover)
-            return set_error(WL_ERR_STATE, "the decomposed operator has no clover term");
         const char *o = (const char*)out[d], *i = (const char*)in[d];
         if (o < i + fb && i < o + fb) return set_error(WL_ERR_ARG, "out and in overlap");
     }
@@ -749,6 +811,7 @@ extern "C" int wilson_mult_dd(wl_dd dd, void* const* out, const void* const* in,
     cudaStream_t s = (cudaStream_t)stream;
     const size_t fb = spinor_field_bytes(prec, dd->gloc.Vh);
     const double kappa = dd->global.kappa;
+    const bool clov = dd->dom[0]->has_clover;
     if (!eo) {  // out_p = in_p - kappa H in_{1-p} on [even | odd] block fields
         DDLaunch h;
         h.prec = prec;
@@ -761,10 +824,19 @@ extern "C" int wilson_mult_dd(wl_dd dd, void* const* out, const void* const* in,
             h.in[d][1] = in[d];
             h.out[d][0] = out[d];
             h.out[d][1] = (char*)out[d] + fb;
-            h.x1[d][0] = in[d];
-            h.x1[d][1] = (const char*)in[d] + fb;
+            if (clov) {  // out_p = A_pp in_p - kappa H in_{1-p}
+                h.x2[d][0] = in[d];
+                h.x2[d][1] = (const char*)in[d] + fb;
+            } else {
+                h.x1[d][0] = in[d];
+                h.x1[d][1] = (const char*)in[d] + fb;
+            }
         }
-        h.rs_in = h.rs_out = h.rs_x1 = (long long)(2 * fb);
+        h.rs_in = h.rs_out = h.rs_x1 = h.rs_x2 = (long long)(2 * fb);
+        if (clov) {
+            h.b1 = 1.0;
+            h.cl_mode = kClX2;
+        }
         h.a = -kappa;
         return dd_launch_hop(dd, h, s);
     }
@@ -780,15 +852,23 @@ extern "C" int wilson_mult_dd(wl_dd dd, void* const* out, const void* const* in,
         h1.out[d][0] = dd->dom[d]->tmp[prec];
     }
     h1.rs_in = h1.rs_out = (long long)fb;
+    if (clov) h1.cl_mode = kClOut;  // tmp = A_oo^-1 H_oe in
     WL_TRY(dd_launch_hop(dd, h1, s));
     DDLaunch h2 = h1;
     h2.parity0 = 0;
     for (int d = 0; d < dd->ndom; ++d) {
         h2.in[d][0] = dd->dom[d]->tmp[prec];
         h2.out[d][0] = out[d];
-        h2.x1[d][0] = in[d];
+        if (clov) h2.x2[d][0] = in[d];  // out = A_ee in - kappa^2 H_eo tmp
+        else h2.x1[d][0] = in[d];
     }
-    h2.rs_x1 = (long long)fb;
+    h2.rs_x1 = h2.rs_x2 = (long long)fb;
+    if (clov) {
+        h2.b1 = 1.0;
+        h2.cl_mode = kClX2;
+    } else {
+        h2.cl_mode = kClNone;
+    }
     h2.a = -kappa * kappa;
     return dd_launch_hop(dd, h2, s);
 }

@@ -1,9 +1,11 @@
 // Kernels of the domain-decomposed hopping term (dd.cuh): face packing,
 // interior and boundary sweeps, and the sum over the blocks.  Templates over
-// precision P, dagger DAG, fused reduction DOT, link format LF and the site
-// set (BND: boundary sites, whose hops may read the halo).  dd_hop.cu
-// instantiates LF = 0 (all nine entries per link), dd_hop_r12.cu LF = 1
-// (two-row compressed links), so the two compile in parallel.
+// precision P, dagger DAG, fused reduction DOT, link format LF, clover mode CL
+// (the epilogue's, as in hop.cuh) and the site set (BND: boundary sites, whose
+// hops may read the halo).  Each translation unit instantiates one (LF, CL)
+// family, so they compile in parallel: dd_hop.cu (LF = 0, no clover, and the
+// pack kernel), dd_hop_r12.cu (LF = 1), dd_hop_clover.cu and
+// dd_hop_r12_clover.cu (the two clover modes).
 #pragma once
 
 #include "dd.cuh"
@@ -13,7 +15,7 @@ namespace wl {
 
 static constexpr int kDDBlock = 128;
 
-template <int P, bool DAG, bool DOT, int LF, bool BND>
+template <int P, bool DAG, bool DOT, int LF, bool BND, int CL>
 __global__ void __launch_bounds__(kDDBlock, (MinBlocks<P, DOT>::value * 2)) dd_hop_kernel(const DDArgs A)
 {
     using T = typename Prec<P>::real;
@@ -47,8 +49,8 @@ __global__ void __launch_bounds__(kDDBlock, (MinBlocks<P, DOT>::value * 2)) dd_h
         cx<T> acc[12];
         dd_hop_site<P, DAG, LF, BND>(acc, A, D.in[pidx] + rhs * A.rs_in, D.links[pidx], i, nb, cross, remote, halo, f);
         auto at = [&](const char* q, long long rs) -> const char* { return q ? q + rhs * rs : nullptr; };
-        epilogue_ptrs<P, DOT, kClNone>(acc, A.a, at(D.x1[pidx], A.rs_x1), at(D.x2[pidx], A.rs_x2), A.b1,
-                                       at(D.w[pidx], A.rs_w), D.out[pidx] + rhs * A.rs_out, A.g.Vh, i, part);
+        epilogue_ptrs<P, DOT, CL>(acc, A.a, at(D.x1[pidx], A.rs_x1), at(D.x2[pidx], A.rs_x2), A.b1,
+                                  at(D.w[pidx], A.rs_w), D.out[pidx] + rhs * A.rs_out, A.g.Vh, i, part, D.cl[pidx]);
     }
     if constexpr (DOT) {
         typename RedType<T>::type wp[3] = {(typename RedType<T>::type)part[0], (typename RedType<T>::type)part[1],
@@ -117,56 +119,44 @@ __global__ void __launch_bounds__(kDDBlock) dd_pack_kernel(const DDPackArgs A)
                   S.count, f, h0, h1, nrm);
 }
 
-// Launchers of one link format (LF = 1 exists for FP32 / FP16 only).
-template <int LF>
+// Launchers of one link format and clover mode (LF = 1 exists for FP32 /
+// FP16 only).
+template <int LF, int CL>
 struct DDKernels {
     static void hop(int prec, bool dagger, bool dot, bool bnd, const DDArgs& A, dim3 grid, cudaStream_t s);
-    static void pack(int prec, bool dagger, const DDPackArgs& A, dim3 grid, cudaStream_t s);
 };
 
-template <int LF, int P, bool BND>
+// The packed half spinor depends on neither (dd_hop.cu).
+void dd_pack(int prec, bool dagger, const DDPackArgs& A, dim3 grid, cudaStream_t s);
+
+template <int LF, int CL, int P, bool BND>
 static void dd_hop_p(bool dagger, bool dot, const DDArgs& A, dim3 grid, cudaStream_t s)
 {
     if (dagger) {
-        if (dot) dd_hop_kernel<P, true, true, LF, BND><<<grid, kDDBlock, 0, s>>>(A);
-        else dd_hop_kernel<P, true, false, LF, BND><<<grid, kDDBlock, 0, s>>>(A);
+        if (dot) dd_hop_kernel<P, true, true, LF, BND, CL><<<grid, kDDBlock, 0, s>>>(A);
+        else dd_hop_kernel<P, true, false, LF, BND, CL><<<grid, kDDBlock, 0, s>>>(A);
     } else {
-        if (dot) dd_hop_kernel<P, false, true, LF, BND><<<grid, kDDBlock, 0, s>>>(A);
-        else dd_hop_kernel<P, false, false, LF, BND><<<grid, kDDBlock, 0, s>>>(A);
+        if (dot) dd_hop_kernel<P, false, true, LF, BND, CL><<<grid, kDDBlock, 0, s>>>(A);
+        else dd_hop_kernel<P, false, false, LF, BND, CL><<<grid, kDDBlock, 0, s>>>(A);
     }
 }
 
-template <int LF, int P>
+template <int LF, int CL, int P>
 static void dd_hop_pb(bool dagger, bool dot, bool bnd, const DDArgs& A, dim3 grid, cudaStream_t s)
 {
-    if (bnd) dd_hop_p<LF, P, true>(dagger, dot, A, grid, s);
-    else dd_hop_p<LF, P, false>(dagger, dot, A, grid, s);
+    if (bnd) dd_hop_p<LF, CL, P, true>(dagger, dot, A, grid, s);
+    else dd_hop_p<LF, CL, P, false>(dagger, dot, A, grid, s);
 }
 
-template <int LF>
-void DDKernels<LF>::hop(int prec, bool dagger, bool dot, bool bnd, const DDArgs& A, dim3 grid, cudaStream_t s)
+template <int LF, int CL>
+void DDKernels<LF, CL>::hop(int prec, bool dagger, bool dot, bool bnd, const DDArgs& A, dim3 grid, cudaStream_t s)
 {
-    if (prec == WL_F32) dd_hop_pb<LF, WL_F32>(dagger, dot, bnd, A, grid, s);
-    else if (prec == WL_F16) dd_hop_pb<LF, WL_F16>(dagger, dot, bnd, A, grid, s);
+    if (prec == WL_F32) dd_hop_pb<LF, CL, WL_F32>(dagger, dot, bnd, A, grid, s);
+    else if (prec == WL_F16) dd_hop_pb<LF, CL, WL_F16>(dagger, dot, bnd, A, grid, s);
     else if constexpr (LF == 0) {
-        if (prec == WL_F64) dd_hop_pb<LF, WL_F64>(dagger, dot, bnd, A, grid, s);
-        else dd_hop_pb<LF, WL_DF64>(dagger, dot, bnd, A, grid, s);
+        if (prec == WL_F64) dd_hop_pb<LF, CL, WL_F64>(dagger, dot, bnd, A, grid, s);
+        else dd_hop_pb<LF, CL, WL_DF64>(dagger, dot, bnd, A, grid, s);
     }
-}
-
-template <int LF>
-void DDKernels<LF>::pack(int prec, bool dagger, const DDPackArgs& A, dim3 grid, cudaStream_t s)
-{
-    // the packed half spinor does not depend on the link format
-    auto go = [&](auto pc) {
-        constexpr int PP = decltype(pc)::value;
-        if (dagger) dd_pack_kernel<PP, true><<<grid, kDDBlock, 0, s>>>(A);
-        else dd_pack_kernel<PP, false><<<grid, kDDBlock, 0, s>>>(A);
-    };
-    if (prec == WL_F32) go(std::integral_constant<int, WL_F32>());
-    else if (prec == WL_F16) go(std::integral_constant<int, WL_F16>());
-    else if (prec == WL_F64) go(std::integral_constant<int, WL_F64>());
-    else go(std::integral_constant<int, WL_DF64>());
 }
 
 }  // namespace wl

@@ -275,7 +275,7 @@ static int dd_ensure_ws(wl_dd dd, int inner, int nrhs)
         WL_TRY(dd_alloc(w, (void**)&w->b64[d], 2 * w->hb64 * n));
         WL_TRY(dd_alloc(w, (void**)&w->bp[d], w->hb64 * n));
         WL_TRY(dd_alloc(w, (void**)&w->xhi[d], 2 * w->hb64 * n));
-        WL_TRY(dd_alloc(w, (void**)&w->rhi[d], w->hb64 * n));
+        WL_TRY(dd_alloc(w, (void**)&w->rhi[d], 2 * w->hb64 * n));  // both halves: the clover final check
         WL_TRY(dd_alloc(w, (void**)&w->tmp64[d], w->hb64 * n));
         if (w->outer == WL_F64) {
             w->bout[d] = w->b64[d];
@@ -371,17 +371,26 @@ static int dd_apply_A(wl_dd dd, DDSolveWork* w, void* const* out, void* const* i
     }
     h1.rs_in = h1.rs_out = (long long)hb;
     h1.active_stride = kActiveStride;
+    const bool clov = dd->dom[0]->has_clover;
+    if (clov) h1.cl_mode = kClOut;  // tmp = A_oo^-1 H_oe in
     WL_TRY(dd_launch_hop(dd, h1, s));
     DDLaunch h2 = h1;
     h2.parity0 = 0;
     for (int d = 0; d < dd->ndom; ++d) {
         h2.in[d][0] = w->tmp[d];
         h2.out[d][0] = out[d];
-        h2.x1[d][0] = in[d];
+        if (clov) h2.x2[d][0] = in[d];  // out = A_ee in - kappa^2 H_eo tmp
+        else h2.x1[d][0] = in[d];
         h2.w[d][0] = wdot[d];
         h2.dot_out[d] = (double*)((char*)w->sc[d] + scal_off);
     }
-    h2.rs_x1 = h2.rs_w = (long long)hb;
+    h2.rs_x1 = h2.rs_x2 = h2.rs_w = (long long)hb;
+    if (clov) {
+        h2.b1 = 1.0;
+        h2.cl_mode = kClX2;
+    } else {
+        h2.cl_mode = kClNone;
+    }
     h2.a = -dd->global.kappa * dd->global.kappa;
     h2.dot = true;
     h2.dot_stride = kScalStride;
@@ -475,9 +484,12 @@ static int dd_residual(wl_dd dd, DDSolveWork* w, int nrhs, cudaStream_t s)
     }
     h1.rs_in = 2 * hb;
     h1.rs_out = hb;
+    const bool clov = dd->dom[0]->has_clover;
+    if (clov) h1.cl_mode = kClOut;  // tmp = A_oo^-1 H_oe x
     WL_TRY(dd_launch_hop(dd, h1, s));
     DDLaunch h2;
     h2.prec = w->outer;
+    if (clov) h2.cl_mode = kClX2;  // r = b' - A_ee x + kappa^2 H_eo tmp
     h2.parity0 = 0;
     h2.nrhs = nrhs;
     for (int d = 0; d < dd->ndom; ++d) {
@@ -588,7 +600,6 @@ extern "C" int wilson_solve_dd(wl_dd dd, double* const* x, const double* const* 
         if (!x[d] || !b[d]) return set_error(WL_ERR_ARG, "NULL block field");
         if (!dd->dom[d]->links[prm->inner][0])
             return set_error(WL_ERR_STATE, "decomposition was created without the inner precision");
-        if (dd->dom[d]->has_clover) return set_error(WL_ERR_STATE, "the decomposed operator has no clover term");
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int P = prm->inner;
@@ -611,7 +622,8 @@ extern "C" int wilson_solve_dd(wl_dd dd, double* const* x, const double* const* 
     WL_TRY(dd_read_norms(w, nrhs, s));
     std::vector<double> bnorm2(nrhs), rnorm2(nrhs), target2(nrhs), true_resid(nrhs, 0.0);
     for (int k = 0; k < nrhs; ++k) bnorm2[k] = w->nrm_h[3 * k + 2];
-    {  // b' = b_e + kappa H_eo b_o (outer precision)
+    const bool clov = dd->dom[0]->has_clover;
+    {  // b' = b_e + kappa H_eo b_o (outer precision; H_eo A_oo^-1 b_o with a clover term)
         DDLaunch h;
         h.prec = w->outer;
         h.parity0 = 0;
@@ -620,8 +632,14 @@ extern "C" int wilson_solve_dd(wl_dd dd, double* const* x, const double* const* 
             h.in[d][0] = (const char*)w->bout[d] + hb;
             h.out[d][0] = w->bp[d];
             h.x1[d][0] = w->bout[d];
+            if (clov) {
+                WL_TRY(launch_clover_apply(dd->dom[d], w->outer, w->tmp64[d], (const char*)w->bout[d] + hb, 1, 1, nrhs,
+                                           s, hb, 2 * hb));
+                h.in[d][0] = w->tmp64[d];
+            }
         }
-        h.rs_in = h.rs_x1 = 2 * hb;
+        h.rs_in = clov ? hb : 2 * hb;
+        h.rs_x1 = 2 * hb;
         h.rs_out = hb;
         h.a = kappa;
         WL_TRY(dd_launch_hop(dd, h, s));
@@ -764,23 +782,32 @@ extern "C" int wilson_solve_dd(wl_dd dd, double* const* x, const double* const* 
             }
             h.rs_in = h.rs_out = h.rs_x1 = 2 * hb;
             h.a = kappa;
+            if (clov) h.cl_mode = kClOut;  // x_o = A_oo^-1 (b_o + kappa H_oe x_e)
             WL_TRY(dd_launch_hop(dd, h, s));
+            // r_p = b_p - A_pp x_p + kappa H x_{1-p}: the even half (the odd one
+            // is zero by construction of x_o); both with a clover term, whose
+            // A_oo^-1 leaves a rounding-level odd residual
             DDLaunch r;
             r.prec = WL_F64;
             r.parity0 = 0;
+            r.nparity = clov ? 2 : 1;
             r.nrhs = nrhs;
             for (int d = 0; d < nd; ++d) {
                 r.in[d][0] = (const char*)w->x64[d] + hb;
+                r.in[d][1] = w->x64[d];
                 r.out[d][0] = w->rhi[d];
+                r.out[d][1] = (char*)w->rhi[d] + hb;
                 r.x1[d][0] = w->b64[d];
+                r.x1[d][1] = (const char*)w->b64[d] + hb;
                 r.x2[d][0] = w->x64[d];
+                r.x2[d][1] = (const char*)w->x64[d] + hb;
                 r.dot_out[d] = w->nrm[d];
             }
-            r.rs_in = r.rs_x1 = r.rs_x2 = 2 * hb;
-            r.rs_out = hb;
+            r.rs_in = r.rs_x1 = r.rs_x2 = r.rs_out = 2 * hb;
             r.b1 = -1.0;
             r.a = kappa;
             r.dot = true;
+            if (clov) r.cl_mode = kClX2;
             WL_TRY(dd_launch_hop(dd, r, s));
         }
         WL_TRY(dd_read_norms(w, nrhs, s));

@@ -144,6 +144,9 @@ struct HopLaunch {
 int launch_hop(wl_gauge g, const HopLaunch& h, cudaStream_t s);
 
 // record-or-not helpers for per-launch timing
+// Attach the clover field F (canonical FP64, device; NULL detaches) to g:
+// wl_clover_set without its entry checks.
+int clover_set(wl_gauge g, const double* F, cudaStream_t s);
 void timing_begin(wl_gauge g, cudaStream_t s, double bytes, int prec, int* slot);
 void timing_end(wl_gauge g, cudaStream_t s, int slot);
 // Solver graphs: launches captured between timing_capture_begin and

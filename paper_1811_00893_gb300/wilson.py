@@ -108,6 +108,7 @@ def load() -> ctypes.CDLL:
             "wl_dd_set_exchange": (I, [P, I]),
             "wl_dd_scatter": (I, [P, P, P, I, P]),
             "wl_dd_gather": (I, [P, P, P, I, P]),
+            "wl_dd_clover_set": (I, [P, P, P]),
             "wilson_dslash_dd": (I, [P, P, P, I, I, I, I, P]),
             "wilson_mult_dd": (I, [P, P, P, I, I, I, I, P]),
             "wl_cdot_dd": (I, [P, P, P, P, I, I, P]),
@@ -134,7 +135,7 @@ def exported_symbols():
             "wl_field_to_internal", "wl_field_to_canonical", "wilson_dslash", "wilson_mult",
             "wl_clover_set", "wl_clover_apply", "wl_cdot", "wl_cdot_noalloc", "wilson_solve",
             "wilson_solve_batch", "wl_dd_create", "wl_dd_create_part", "wl_dd_plan", "wl_dd_destroy", "wl_dd_blocks", "wl_dd_block",
-            "wl_dd_set_exchange", "wl_dd_scatter", "wl_dd_gather", "wilson_dslash_dd",
+            "wl_dd_set_exchange", "wl_dd_scatter", "wl_dd_gather", "wl_dd_clover_set", "wilson_dslash_dd",
             "wilson_mult_dd", "wl_cdot_dd", "wilson_solve_dd", "wl_last_error",
             "wl_spinor16_format",
             "wl_launch_count", "wl_algorithmic_bytes", "wl_timing", "wl_timing_read"]
@@ -329,6 +330,11 @@ def wl_dd_scatter(dd, local, glob, nrhs: int, stream=None) -> None:
 
 def wl_dd_gather(dd, glob, local, nrhs: int, stream=None) -> None:
     _check(load().wl_dd_gather(dd, _ptr(glob), _ptrs(local), int(nrhs), _stream(stream)))
+
+
+def wl_dd_clover_set(dd, F, stream=None) -> None:
+    """Attach the clover term F of the whole lattice to every held block (None detaches)."""
+    _check(load().wl_dd_clover_set(dd, _ptr(F), _stream(stream)))
 
 
 def wilson_dslash_dd(dd, out, inp, out_parity: int, dagger: int, prec: int, nrhs: int,

@@ -290,6 +290,115 @@ def test_dd_errors():
 
 
 # ----------------------------------------------------------------------------
+# the clover term (Eq. 2) on the decomposed lattice
+# ----------------------------------------------------------------------------
+
+CLOVER_CASES = [((4, 4, 4, 8), (1, 1, 1, 2), (1, 1, 1, -1)),
+                ((4, 4, 8, 8), (1, 1, 2, 2), (1, np.exp(0.2j), 1, TW))]
+
+
+@pytest.fixture(scope="module", params=CLOVER_CASES,
+                ids=lambda c: "x".join(map(str, c[0])) + "-g" + "".join(map(str, c[1])))
+def cdd(request):
+    dims, grid, bc = request.param
+    c = DDCase(dims, grid, bc)
+    c.F = fields.clover_field(dims, 57).numpy()
+    c.F_dev = torch.from_numpy(c.F).cuda().contiguous()
+    wilson.wl_dd_clover_set(c.dd.handle, c.F_dev)
+    c.g = wilson.Gauge(dims, c.kappa, c.U_dev, precs=("f64", "f32", "f16"), bc=bc)
+    wilson.wl_clover_set(c.g.handle, c.F_dev)
+    yield c
+    c.g.close()
+    c.close()
+
+
+def _full_internal(g, psi, prec):
+    nrhs = psi.shape[0]
+    fb = wilson.wl_field_bytes(g.handle, PRECS[prec], 1)
+    out = torch.empty(2 * fb * nrhs, dtype=torch.uint8, device="cuda")
+    for r in range(nrhs):
+        for p in (0, 1):
+            wilson.wl_field_to_internal(g.handle, out[(2 * r + p) * fb:(2 * r + p + 1) * fb], psi[r:r + 1], p,
+                                        PRECS[prec], 1)
+    return out, fb
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "df64"])
+@pytest.mark.parametrize("dagger", [0, 1])
+def test_clover_mult_dd_equals_undivided(cdd, prec, dagger):
+    """M_ee = A_ee - kappa^2 H_eo A_oo^-1 H_oe and D_clov on the decomposed
+    lattice run the undivided operator's fused clover epilogues on every
+    site: bit for bit the undivided results (which the clover tests hold
+    against the oracle); M_ee also against the oracle here."""
+    nrhs = 1
+    psi = fields.gaussian_fermion(cdd.dims, nrhs, 33).cuda()
+    g = cdd.g
+    inp = g.field(prec, nrhs)
+    wilson.wl_field_to_internal(g.handle, inp, psi, 0, PRECS[prec], nrhs)
+    out = g.field(prec, nrhs)
+    wilson.wilson_mult(g.handle, out, inp, 1, dagger, PRECS[prec], nrhs)
+    ref = torch.zeros((nrhs, cdd.V, 4, 3), dtype=torch.complex128, device="cuda")
+    wilson.wl_field_to_canonical(g.handle, ref, out, 0, PRECS[prec], nrhs)
+    dout = cdd.dd.field(prec, nrhs)
+    wilson.wilson_mult_dd(cdd.dd.handle, dout, cdd.to_blocks(psi, 0, prec), 1, dagger, PRECS[prec], nrhs)
+    got = cdd.from_blocks(dout, 0, prec, nrhs)
+    assert torch.equal(got, ref), ("Mee", rel(cdd.half(got, 0), cdd.half(ref, 0)))
+    if dagger == 0:
+        want = oracle.clover_Mee(cdd.U, cdd.F, cdd.half(psi, 0), cdd.dims, cdd.bc, cdd.kappa)
+        assert rel(cdd.half(got, 0), want) <= TOL[prec]
+    # eo = 0: D_clov on [even | odd] fields
+    inp, fb = _full_internal(g, psi, prec)
+    out = torch.empty_like(inp)
+    wilson.wilson_mult(g.handle, out, inp, 0, dagger, PRECS[prec], nrhs)
+    ref = torch.zeros((nrhs, cdd.V, 4, 3), dtype=torch.complex128, device="cuda")
+    for p in (0, 1):
+        wilson.wl_field_to_canonical(g.handle, ref, out[p * fb:(p + 1) * fb], p, PRECS[prec], 1)
+    dout = cdd.dd.field(prec, nrhs, nhalf=2)
+    wilson.wilson_mult_dd(cdd.dd.handle, dout, cdd.to_blocks_full(psi, prec), 0, dagger, PRECS[prec], nrhs)
+    got = cdd.from_blocks_full(dout, prec, nrhs)
+    assert torch.equal(got, ref), ("D", rel(got[0].cpu().numpy(), ref[0].cpu().numpy()))
+
+
+@pytest.mark.parametrize("inner,delta", [("f32", 0.0), ("f64", 0.0), ("f16", 0.003)],
+                         ids=["f32-defect-correction", "f64", "f16-reliable"])
+def test_clover_solve_dd_reaches_oracle_residual(cdd, inner, delta):
+    nrhs = 2
+    b = fields.gaussian_fermion(cdd.dims, nrhs, 53).cuda()
+    bl = cdd.dd.canonical(nrhs)
+    wilson.wl_dd_scatter(cdd.dd.handle, bl, b, nrhs)
+    xl = cdd.dd.canonical(nrhs)
+    prm = wilson.solve_params(tol=1e-10, eo=True, inner=PRECS[inner], delta=delta)
+    rc, info = wilson.wilson_solve_dd(cdd.dd.handle, xl, bl, nrhs, prm)
+    x = torch.zeros_like(b)
+    wilson.wl_dd_gather(cdd.dd.handle, x, xl, nrhs)
+    for r in range(nrhs):
+        tr = oracle.clover_true_residual(cdd.U, cdd.F, b[r].cpu().numpy(), x[r].cpu().numpy(), cdd.dims, cdd.bc,
+                                         cdd.kappa)
+        assert tr <= 1e-10, (inner, r, tr, info[r])
+        assert info[r]["status"] == 0 and info[r]["true_resid"] <= 1e-10
+
+
+def test_clover_set_dd_errors_leave_no_term():
+    c = DDCase((4, 4, 4, 8), (1, 1, 1, 2), (1, 1, 1, -1))
+    try:
+        F = fields.clover_field(c.dims, 5).numpy()
+        F[3, 0, 1, 2] += 0.5  # no longer Hermitian
+        with pytest.raises(wilson.WilsonError) as e:
+            wilson.wl_dd_clover_set(c.dd.handle, torch.from_numpy(F).cuda().contiguous())
+        assert e.value.code == wilson.WL_ERR_ARG
+        psi = fields.gaussian_fermion(c.dims, 1, 7).cuda()
+        got = _mee_blocks(c, psi, "f64")  # the Wilson operator: no block kept a term
+        want = oracle.Mee(c.U, c.half(psi, 0), c.dims, c.bc, c.kappa)
+        assert rel(c.half(got, 0), want) <= TOL["f64"]
+        g = c.dd.blocks[0][0]
+        with pytest.raises(wilson.WilsonError) as e:
+            wilson.wl_clover_set(g, torch.from_numpy(F).cuda().contiguous())
+        assert e.value.code == wilson.WL_ERR_STATE  # blocks take the term through the decomposition
+    finally:
+        c.close()
+
+
+# ----------------------------------------------------------------------------
 # the transport path: faces and sums through wl_dd_transport callbacks
 # ----------------------------------------------------------------------------
 
