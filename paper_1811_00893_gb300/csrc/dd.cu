@@ -359,8 +359,11 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
     const bool t_only = dd->cut == (1 << 3);
     const int bi = (int)((dd->nint + kDDBlock - 1) / kDDBlock);
     const int bb = (int)((dd->nbnd + kDDBlock - 1) / kDDBlock);
+    // reducing launches: capped grids looping over both parities' sites
+    const int gi = h.dot && dd->nint ? dd_reducing_grid(np * dd->nint, dd->ndom, dd->dom[0]->num_sms) : 0;
+    const int gb = h.dot && dd->nbnd ? dd_reducing_grid(np * dd->nbnd, dd->ndom, dd->dom[0]->num_sms) : 0;
     if (h.dot) {
-        WL_TRY(ensure_partials(dd, nrhs, np * (bi + bb)));
+        WL_TRY(ensure_partials(dd, nrhs, gi + gb));
         A.partial = dd->partial;
         A.dom_stride = dd->part_dom_stride;
         A.max_blocks = dd->part_max_blocks;
@@ -375,9 +378,11 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
         AA.sites = part ? dd->bsites : (t_only ? nullptr : dd->isites);
         AA.site0 = (!part && t_only) ? g.st : 0;
         AA.nsites = n;
+        AA.nparity = np;
         AA.blocks_per_parity = part ? bb : bi;
-        AA.block0 = part ? np * bi : 0;
-        const dim3 grid((unsigned)(AA.blocks_per_parity * np), (unsigned)nrhs, (unsigned)dd->ndom);
+        AA.block0 = h.dot ? (part ? gi : 0) : (part ? np * bi : 0);
+        const unsigned gx = h.dot ? (unsigned)(part ? gb : gi) : (unsigned)(AA.blocks_per_parity * np);
+        const dim3 grid(gx, (unsigned)nrhs, (unsigned)dd->ndom);
         dd_hop_family(lf, h.cl_mode, P, h.dagger != 0, h.dot, part == 1, AA, grid, st_);
         WL_CHECK_LAUNCH((double)dd->ndom * np * n * site_bytes);
         return WL_OK;
@@ -449,7 +454,7 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
         F.partial = dd->partial;
         F.dom_stride = dd->part_dom_stride;
         F.max_blocks = dd->part_max_blocks;
-        F.nblocks = np * (bi + bb);
+        F.nblocks = gi + gb;
         F.ndom = dd->ndom;
         for (int d = 0; d < dd->ndom; ++d) F.out[d] = h.dot_out[d];
         F.out_stride = h.dot_stride;

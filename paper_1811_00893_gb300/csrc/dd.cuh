@@ -180,8 +180,8 @@ struct DDArgs {
     const int* sites;      // the launch's sites: interior or boundary half indices, or
     long long site0;       // (sites == nullptr) the contiguous range site0 .. site0 + nsites - 1
     long long nsites;
-    int blocks_per_parity;
-    int parity0;
+    int blocks_per_parity;  // plain launches: one site per thread, a block's parity fixed
+    int parity0, nparity;   // launches with a fused reduction loop over both parities' sites
     long long rs_in, rs_out, rs_x1, rs_x2, rs_w;
     double a, b1;
     cx<float> ph[4];

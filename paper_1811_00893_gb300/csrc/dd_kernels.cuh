@@ -15,6 +15,47 @@ namespace wl {
 
 static constexpr int kDDBlock = 128;
 
+// Output site j of the launch's site set, launch parity pidx: the hopping
+// term (halo reads on boundary sites) and the epilogue; with DOT its (w, out),
+// ||out||^2 are added to part.
+template <int P, bool DAG, bool DOT, int LF, bool BND, int CL>
+__device__ __forceinline__ void dd_site(const DDArgs& A, const DDDom& D, int rhs, int pidx, long long j,
+                                        typename Prec<P>::real (&part)[3])
+{
+    using T = typename Prec<P>::real;
+    const int i = A.sites ? A.sites[j] : (int)(A.site0 + j);
+    const int p = A.parity0 + pidx;
+    int c[4], xh, nb[8];
+    half_coords(A.g, p, i, c, xh);
+    const unsigned faces = block_neighbours(A.g, i, c, xh, nb);
+    const unsigned cross = faces & D.edge;  // hops that cross the global boundary
+    const char* halo[4][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    long long f[4] = {0, 0, 0, 0};
+    unsigned remote = 0;
+    if constexpr (BND) {
+        remote = faces & A.cutmask;
+#pragma unroll
+        for (int mu = 1; mu < 4; ++mu)
+            if (A.fs[mu]) {
+                f[mu] = face_index(A.g, mu, c, xh);
+                const long long seg_rs = halo_face_bytes(P, A.fs[mu]);
+                halo[mu][0] = D.halo + A.hoff[pidx][mu][0] + rhs * seg_rs;
+                halo[mu][1] = D.halo + A.hoff[pidx][mu][1] + rhs * seg_rs;
+            }
+    }
+    cx<T> acc[12];
+    dd_hop_site<P, DAG, LF, BND>(acc, A, D.in[pidx] + rhs * A.rs_in, D.links[pidx], i, nb, cross, remote, halo, f);
+    auto at = [&](const char* q, long long rs) -> const char* { return q ? q + rhs * rs : nullptr; };
+    T pt[3] = {0, 0, 0};
+    epilogue_ptrs<P, DOT, CL>(acc, A.a, at(D.x1[pidx], A.rs_x1), at(D.x2[pidx], A.rs_x2), A.b1,
+                              at(D.w[pidx], A.rs_w), D.out[pidx] + rhs * A.rs_out, A.g.Vh, i, pt, D.cl[pidx]);
+    if (DOT)
+        for (int k = 0; k < 3; ++k) part[k] += pt[k];
+}
+
+// Plain launches: one site per thread, grid.x = blocks_per_parity x parities.
+// Launches with a fused reduction: a capped grid loops over the sites of both
+// parities, so the per-block partials the finishing launch adds up are few.
 template <int P, bool DAG, bool DOT, int LF, bool BND, int CL>
 __global__ void __launch_bounds__(kDDBlock, (MinBlocks<P, DOT>::value * 2)) dd_hop_kernel(const DDArgs A)
 {
@@ -22,37 +63,18 @@ __global__ void __launch_bounds__(kDDBlock, (MinBlocks<P, DOT>::value * 2)) dd_h
     const int rhs = blockIdx.y, dom = blockIdx.z;
     const DDDom& D = A.d[dom];
     if (D.active && D.active[(long long)rhs * A.active_stride] == 0) return;  // uniform per block
-    const int pidx = blockIdx.x / A.blocks_per_parity;
-    const long long j = (long long)(blockIdx.x - pidx * A.blocks_per_parity) * kDDBlock + threadIdx.x;
     T part[3] = {0, 0, 0};
-    if (j < A.nsites) {
-        const int i = A.sites ? A.sites[j] : (int)(A.site0 + j);
-        const int p = A.parity0 + pidx;
-        int c[4], xh, nb[8];
-        half_coords(A.g, p, i, c, xh);
-        const unsigned faces = block_neighbours(A.g, i, c, xh, nb);
-        const unsigned cross = faces & D.edge;  // hops that cross the global boundary
-        const char* halo[4][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
-        long long f[4] = {0, 0, 0, 0};
-        unsigned remote = 0;
-        if constexpr (BND) {
-            remote = faces & A.cutmask;
-#pragma unroll
-            for (int mu = 1; mu < 4; ++mu)
-                if (A.fs[mu]) {
-                    f[mu] = face_index(A.g, mu, c, xh);
-                    const long long seg_rs = halo_face_bytes(P, A.fs[mu]);
-                    halo[mu][0] = D.halo + A.hoff[pidx][mu][0] + rhs * seg_rs;
-                    halo[mu][1] = D.halo + A.hoff[pidx][mu][1] + rhs * seg_rs;
-                }
+    if constexpr (!DOT) {
+        const int pidx = blockIdx.x / A.blocks_per_parity;
+        const long long j = (long long)(blockIdx.x - pidx * A.blocks_per_parity) * kDDBlock + threadIdx.x;
+        if (j < A.nsites) dd_site<P, DAG, DOT, LF, BND, CL>(A, D, rhs, pidx, j, part);
+    } else {
+        const long long total = (long long)A.nparity * A.nsites;
+        for (long long q = blockIdx.x * (long long)kDDBlock + threadIdx.x; q < total;
+             q += (long long)gridDim.x * kDDBlock) {
+            const int pidx = q >= A.nsites ? 1 : 0;
+            dd_site<P, DAG, DOT, LF, BND, CL>(A, D, rhs, pidx, q - pidx * A.nsites, part);
         }
-        cx<T> acc[12];
-        dd_hop_site<P, DAG, LF, BND>(acc, A, D.in[pidx] + rhs * A.rs_in, D.links[pidx], i, nb, cross, remote, halo, f);
-        auto at = [&](const char* q, long long rs) -> const char* { return q ? q + rhs * rs : nullptr; };
-        epilogue_ptrs<P, DOT, CL>(acc, A.a, at(D.x1[pidx], A.rs_x1), at(D.x2[pidx], A.rs_x2), A.b1,
-                                  at(D.w[pidx], A.rs_w), D.out[pidx] + rhs * A.rs_out, A.g.Vh, i, part, D.cl[pidx]);
-    }
-    if constexpr (DOT) {
         typename RedType<T>::type wp[3] = {(typename RedType<T>::type)part[0], (typename RedType<T>::type)part[1],
                                            (typename RedType<T>::type)part[2]};
         warp_sum<3>(wp);
@@ -125,6 +147,15 @@ template <int LF, int CL>
 struct DDKernels {
     static void hop(int prec, bool dagger, bool dot, bool bnd, const DDArgs& A, dim3 grid, cudaStream_t s);
 };
+
+// Blocks of a launch with a fused reduction: about four resident 128-thread
+// blocks per SM, shared by the held blocks, at most one per 128 sites.
+inline int dd_reducing_grid(long long sites, int ndom, int num_sms)
+{
+    const long long need = (sites + kDDBlock - 1) / kDDBlock;
+    const long long g = std::max<long long>(1, 4LL * num_sms / std::max(1, ndom));
+    return (int)std::max<long long>(1, std::min(need, g));
+}
 
 // The packed half spinor depends on neither (dd_hop.cu).
 void dd_pack(int prec, bool dagger, const DDPackArgs& A, dim3 grid, cudaStream_t s);

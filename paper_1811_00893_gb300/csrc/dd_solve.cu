@@ -74,7 +74,8 @@ struct DDVecs {
     Scal* sc[kMaxDomains];
     double* part;
     long long part_dom_stride;
-    int part_blocks;
+    int part_blocks;  // partial slots per right-hand side (allocated)
+    int nparts;       // partials the x/r update leaves (its grid.x)
 };
 
 // p = r + beta (p - omega v):  a = p, b = r, c = v
@@ -138,12 +139,13 @@ __global__ void __launch_bounds__(kDDVec) dd_update_xr_kernel(const DDVecs V)
     __syncthreads();
     using T = typename Prec<P>::real;
     const double dc[4] = {dcoef[0], dcoef[1], dcoef[2], dcoef[3]};
-    T pt[3] = {0, 0, 0};
-    const long long i = blockIdx.x * (long long)kDDVec + threadIdx.x;
-    if (i < V.Vh) {
-        const long long o = rhs * V.rs;
+    T pt[3] = {0, 0, 0};  // a grid of resident blocks loops over the sites: few partials
+    const long long o = rhs * V.rs;
+    for (long long i = blockIdx.x * (long long)kDDVec + threadIdx.x; i < V.Vh; i += (long long)gridDim.x * kDDVec) {
+        T q[3];
         xr_update_site<P, PX>(V.x[dom] + rhs * V.rsx, V.a[dom] + o, V.b[dom] + o, V.c[dom] + o, V.d[dom] + o,
-                              V.e[dom] + o, V.Vh, i, dc, pt);
+                              V.e[dom] + o, V.Vh, i, dc, q);
+        for (int k = 0; k < 3; ++k) pt[k] += q[k];
     }
     typename RedType<T>::type wp[3] = {(typename RedType<T>::type)pt[0], (typename RedType<T>::type)pt[1],
                                        (typename RedType<T>::type)pt[2]};
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(256) dd_advance_kernel(const DDVecs V, int ndo
     } else {
         for (int d = 0; d < ndom; ++d) {
             double v[3];
-            sum_partials<3>(V.part + d * V.part_dom_stride + (long long)rhs * V.part_blocks * 3, V.part_blocks, v);
+            sum_partials<3>(V.part + d * V.part_dom_stride + (long long)rhs * V.part_blocks * 3, V.nparts, v);
             block_sum<3>(v, sh);
             if (threadIdx.x == 0)
                 for (int k = 0; k < 3; ++k) tot[k] += v[k];
@@ -408,6 +410,7 @@ static DDVecs dd_vecs(wl_dd dd, DDSolveWork* w)
     V.part = w->part;
     V.part_dom_stride = w->part_dom_stride;
     V.part_blocks = w->part_blocks;
+    V.nparts = std::max(1, std::min(w->part_blocks, 4 * dd->dom[0]->num_sms / std::max(1, dd->ndom)));
     return V;
 }
 
@@ -449,8 +452,9 @@ static int dd_iteration(wl_dd dd, DDSolveWork* w, int nrhs, cudaStream_t s)
     }
     WL_TRY(dd_dispatch(P, [&](auto pc) -> int {
         constexpr int PP = decltype(pc)::value;
-        if (w->xlo_prec == WL_F64) dd_update_xr_kernel<PP, WL_F64><<<grid, kDDVec, 0, s>>>(V);
-        else dd_update_xr_kernel<PP, WL_F32><<<grid, kDDVec, 0, s>>>(V);
+        const dim3 rgrid((unsigned)V.nparts, grid.y, grid.z);
+        if (w->xlo_prec == WL_F64) dd_update_xr_kernel<PP, WL_F64><<<rgrid, kDDVec, 0, s>>>(V);
+        else dd_update_xr_kernel<PP, WL_F32><<<rgrid, kDDVec, 0, s>>>(V);
         WL_CHECK_LAUNCH((5.0 * w->vb + 2.0 * V.rsx) * nrhs * dd->ndom);
         return WL_OK;
     }));
