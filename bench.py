@@ -403,6 +403,9 @@ def measure_single(wl, rank, world, local, steps, warmup, *, e2e=True, r12=True,
     # the same operator with compressed (two-row) links, measured beside it
     g12 = (wilson.Gauge(wl.dims, wl.kappa, U, precs=("f64", pname), bc=wl.bc, r12=True)
            if pname in ("f32", "f16") and r12 else None)
+    # eight-real links: FP32 single-RHS Wilson launches
+    g8 = (wilson.Gauge(wl.dims, wl.kappa, U, precs=("f64", pname), bc=wl.bc, r8=True)
+          if pname == "f32" and r12 and wl.nrhs == 1 and not wl.clover else None)
     del U
     F_host = None
     if wl.clover:  # D_clov of Eq. 2: attach the seeded synthetic clover field
@@ -517,28 +520,33 @@ def measure_single(wl, rank, world, local, steps, warmup, *, e2e=True, r12=True,
                                 "launches_per_apply": 2}
 
     # ---------------- compressed links: the same Dslash protocol and solve
-    r12_rec = None
-    if g12 is not None:
-        r12_s, _ = time_dslash(lambda: wilson.wilson_dslash(g12.handle, fout, fin, 0, 0, P, nr),
-                               dslash_launches, 1, stream)
-        cb = costs.hop_bytes_per_site(pname, nrhs=nr, r12=True)
-        x12 = torch.zeros_like(b)
-        rc12, inf12 = wilson.wilson_solve(g12.handle, x12, b, wl.nrhs, mixed)  # warm
+    def compressed(gc, cb):
+        t_s, _ = time_dslash(lambda: wilson.wilson_dslash(gc.handle, fout, fin, 0, 0, P, nr),
+                             dslash_launches, 1, stream)
+        xc = torch.zeros_like(b)
+        rcc, infc = wilson.wilson_solve(gc.handle, xc, b, wl.nrhs, mixed)  # warm
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(3):
-            rc12, inf12 = wilson.wilson_solve(g12.handle, x12, b, wl.nrhs, mixed)
+            rcc, infc = wilson.wilson_solve(gc.handle, xc, b, wl.nrhs, mixed)
         f1.record(stream)
         torch.cuda.synchronize()
-        r12_rec = {"dslash_us_per_launch": r12_s * 1e6,
-                   "dslash_gbs_compressed_bytes": cb * Vh / r12_s / 1e9,
-                   "dslash_gbs_equivalent": bps * Vh / r12_s / 1e9,
-                   "dslash_gflops": costs.FLOPS_HOP_SITE * Vh * nr / r12_s / 1e9,
-                   "bytes_per_site_compressed": cb,
-                   "solve_ms": f0.elapsed_time(f1) / 3, "solve_iters": max(i["iters"] for i in inf12),
-                   "solve_true_resid": max(i["true_resid"] for i in inf12)}
+        return {"dslash_us_per_launch": t_s * 1e6,
+                "dslash_gbs_compressed_bytes": cb * Vh / t_s / 1e9,
+                "dslash_gbs_equivalent": bps * Vh / t_s / 1e9,
+                "dslash_gflops": costs.FLOPS_HOP_SITE * Vh * nr / t_s / 1e9,
+                "bytes_per_site_compressed": cb,
+                "solve_ms": f0.elapsed_time(f1) / 3, "solve_iters": max(i["iters"] for i in infc),
+                "solve_true_resid": max(i["true_resid"] for i in infc)}
+
+    r12_rec = r8_rec = None
+    if g12 is not None:
+        r12_rec = compressed(g12, costs.hop_bytes_per_site(pname, nrhs=nr, r12=True))
         g12.close()
+    if g8 is not None:
+        r8_rec = compressed(g8, 8 * 32 + 2 * costs.spinor_bytes(pname))
+        g8.close()
 
     # ---------------- plain FP64 GPU solve for the time-to-solution comparison
     p64 = wilson.solve_params(tol=1e-10, eo=wl.eo, inner=wilson.WL_F64, graph_iters=0)
@@ -603,6 +611,7 @@ def measure_single(wl, rank, world, local, steps, warmup, *, e2e=True, r12=True,
         "roofline": roofline,
         "dslash": dslash,
         "r12": r12_rec,
+        "r8": r8_rec,
         "solve": {"mixed_ms": ms_per_step, "fp64_ms": fp64_ms,
                   "speedup_vs_fp64": fp64_ms / ms_per_step,
                   "mixed_iters": mixed_iters,

@@ -69,6 +69,22 @@ typedef enum { WL_F64 = 0, WL_F32 = 1, WL_F16 = 2, WL_DF64 = 3 } wl_prec;
  * otherwise).  The uneven-batch solver keeps using the full links. */
 #define WL_LINKS_R12 (1 << 8)
 
+/* Flag for wl_gauge_create's prec_mask: also keep the FP32 links in an
+ * eight-real form and use it in single-RHS FP32 hopping launches without a
+ * clover term (256 instead of 576 bytes of links per site).  Per hop matrix:
+ * with its rows taken in the cyclic order that puts the smaller of |U_00|,
+ * |U_10| first, rows (a, b, c), the stored reals are a2, a3, b1 and the
+ * quarter-angle tangents of the phases of a1 and c1 (the first carrying +3
+ * when the order is shifted); the kernel rebuilds the rest from unitarity and
+ * det 1, the boundary phase applied on the fly as for WL_LINKS_R12.  Entries
+ * near zero come back with an absolute error of about the square root of the
+ * FP32 rounding (2.4e-4), the others to FP32 rounding.  Requires SU(3) links
+ * (checked as for WL_LINKS_R12).  Multi-RHS, clover, decomposed and batch
+ * launches keep the other link forms.  On a GB300 the decode costs more than
+ * the bytes it saves (32^3 x 64 FP32 hopping term 127 us, against 96 us with
+ * WL_LINKS_R12 and 119 us with full links), so it is an option, not a default. */
+#define WL_LINKS_R8 (1 << 9)
+
 enum {
     WL_OK = 0,
     WL_ERR_ARG = -1,            /* invalid argument (message says which) */

@@ -22,12 +22,15 @@ extern template struct HopKernels<kClOut, 0>;
 extern template struct HopKernels<kClNone, 1>;
 extern template struct HopKernels<kClX2, 1>;
 extern template struct HopKernels<kClOut, 1>;
+extern template struct HopKernels<kClNone, 2>;  // dslash_r8.cu
 
 // The kernel family of a launch: clover mode and link format.
 template <typename F>
 static void with_variant(const HopLaunch& h, int lf, F&& f)
 {
-    if (lf) {
+    if (lf == 2) {  // eight-real links: Wilson launches only
+        f(HopKernels<kClNone, 2>());
+    } else if (lf) {
         switch (h.cl_mode) {
             case kClX2: f(HopKernels<kClX2, 1>()); break;
             case kClOut: f(HopKernels<kClOut, 1>()); break;
@@ -45,6 +48,7 @@ static void with_variant(const HopLaunch& h, int lf, F&& f)
 // Bytes of the links of one site (all eight hops) in the launch's format.
 static size_t link_site_bytes(int prec, int lf)
 {
+    if (lf == 2) return 256;
     if (lf) return prec == WL_F32 ? 384 : 192;
     return link_field_bytes(prec, 1);
 }
@@ -285,13 +289,15 @@ int launch_hop(wl_gauge g, const HopLaunch& h, cudaStream_t s)
     // compressed links when the gauge object holds them (WL_NO_R12 turns them
     // off, for comparisons)
     static const bool r12_off = getenv("WL_NO_R12") != nullptr;
-    const int lf = (h.prec == WL_F32 || h.prec == WL_F16) && g->links_r12[h.prec][0] && !r12_off ? 1 : 0;
+    int lf = (h.prec == WL_F32 || h.prec == WL_F16) && g->links_r12[h.prec][0] && !r12_off ? 1 : 0;
+    // eight-real links: FP32 single-RHS Wilson launches
+    if (h.prec == WL_F32 && g->links_r8[WL_F32][0] && h.nrhs == 1 && h.cl_mode == kClNone && !r12_off) lf = 2;
     HopArgs A;
     A.g = g->geo;
     A.partials_only = 0;
     for (int k = 0; k < 2; ++k) {
         const int p = h.parity0 + (k < h.nparity ? k : 0);
-        A.links[k] = lf ? g->links_r12[h.prec][p] : g->links[h.prec][p];
+        A.links[k] = lf == 2 ? g->links_r8[h.prec][p] : lf ? g->links_r12[h.prec][p] : g->links[h.prec][p];
         A.cl[k] = h.clov[k];
     }
     for (int mu = 0; mu < 4; ++mu) A.ph[mu] = {(float)g->bc_re[mu], (float)g->bc_im[mu]};

@@ -223,6 +223,23 @@ __device__ double su3_deviation(const double* u)
     return fmax(dev, hypot(det.re - 1.0, det.im));
 }
 
+// The eight reals of an SU(3) matrix w that load_link_r8 (hop.cuh) decodes:
+// rows taken in the cyclic order that puts the smaller of |w_00|, |w_10| first
+// (shifted: (W1, W2, W0)), then a2, a3, b1, tan(arg(a1) / 4) (+ 3 when shifted)
+// and tan(arg(c1) / 4), computed in FP64 and rounded to FP32.
+__device__ void store_link_r8(void* base, long long Vh, int d, long long i, const cx<double> (&w)[9])
+{
+    auto mag2 = [](cx<double> z) { return z.re * z.re + z.im * z.im; };
+    const bool shift = mag2(w[0]) > mag2(w[3]);
+    const cx<double>* a = shift ? w + 3 : w;
+    const cx<double>* b = shift ? w + 6 : w + 3;
+    const cx<double>* c = shift ? w : w + 6;
+    const double ta = tan(0.25 * atan2(a[0].im, a[0].re)), tc = tan(0.25 * atan2(c[0].im, c[0].re));
+    float4* p = (float4*)base + (long long)d * 2 * Vh;
+    p[i] = make_float4((float)a[1].re, (float)a[1].im, (float)a[2].re, (float)a[2].im);
+    p[Vh + i] = make_float4((float)b[0].re, (float)b[0].im, (float)(ta + (shift ? 3.0 : 0.0)), (float)tc);
+}
+
 template <int P>
 __global__ void build_links_r12_kernel(void* out, const double* __restrict__ U, Geom g, Place pl, int p,
                                        int* flag)
@@ -245,6 +262,31 @@ __global__ void build_links_r12_kernel(void* out, const double* __restrict__ U, 
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) w[a * 3 + b] = {v[2 * (b * 3 + a)], -v[2 * (b * 3 + a) + 1]};
         store_link_r12<P>(out, g.Vh, 2 * mu + 1, i, w);
+    }
+}
+
+// Eight-real FP32 links of parity p (hop d = 2 mu: U_mu(x); 2 mu + 1: the
+// daggered backward link), no boundary phase; flag set on a non-SU(3) link.
+__global__ void build_links_r8_kernel(void* out, const double* __restrict__ U, Geom g, Place pl, int p, int* flag)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.Vh) return;
+    int c[4];
+    const long long s = global_site(g, pl, p, i, c);
+    const Geom& G = pl.gl;
+    const long long stride[4] = {1, G.L[0], (long long)G.L[0] * G.L[1],
+                                 (long long)G.L[0] * G.L[1] * G.L[2]};
+    for (int mu = 0; mu < 4; ++mu) {
+        cx<double> w[9];
+        const double* u = U + (s * 4 + mu) * 18;
+        if (su3_deviation(u) > 1e-6) atomicOr(flag, 1);
+        for (int k = 0; k < 9; ++k) w[k] = {u[2 * k], u[2 * k + 1]};
+        store_link_r8(out, g.Vh, 2 * mu, i, w);
+        const long long n = (c[mu] == 0) ? s + (G.L[mu] - 1) * stride[mu] : s - stride[mu];
+        const double* v = U + (n * 4 + mu) * 18;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) w[a * 3 + b] = {v[2 * (b * 3 + a)], -v[2 * (b * 3 + a) + 1]};
+        store_link_r8(out, g.Vh, 2 * mu + 1, i, w);
     }
 }
 
@@ -510,6 +552,35 @@ int gauge_create(wl_gauge* out, const wl_lattice* local, const wl_lattice* globa
                 rc = set_error(WL_ERR_ARG, "WL_LINKS_R12 needs SU(3) links (unitary, det 1, to 1e-6)");
             if (rc != WL_OK) break;
         }
+        if ((prec_mask & WL_LINKS_R8) && (g->prec_mask & WL_PREC_MASK(WL_F32))) {  // eight-real FP32 copies
+            int* flag = nullptr;
+            if (cudaMalloc((void**)&flag, sizeof(int)) != cudaSuccess ||
+                cudaMemsetAsync(flag, 0, sizeof(int), s) != cudaSuccess) {
+                cudaGetLastError();
+                if (flag) cudaFree(flag);
+                rc = set_error(WL_ERR_CUDA, "cudaMalloc for the SU(3) check");
+                break;
+            }
+            for (int p = 0; p < 2 && rc == WL_OK; ++p) {
+                const size_t bytes = 256 * (size_t)g->geo.Vh;
+                if (cudaMalloc(&g->links_r8[WL_F32][p], bytes) != cudaSuccess) {
+                    cudaGetLastError();
+                    rc = set_error(WL_ERR_CUDA, "cudaMalloc eight-real links");
+                    break;
+                }
+                build_links_r8_kernel<<<grid, block, 0, s>>>(g->links_r8[WL_F32][p], U, g->geo, pl, p, flag);
+                if (cudaGetLastError() != cudaSuccess) rc = set_error(WL_ERR_CUDA, "eight-real link build launch");
+                count_launch(1, (double)g->geo.Vh * (8 * 144.0 + 256.0));
+            }
+            int hflag = 0;
+            if (rc == WL_OK && (cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                                cudaStreamSynchronize(s) != cudaSuccess))
+                rc = set_error(WL_ERR_CUDA, "eight-real link build failed");
+            cudaFree(flag);
+            if (rc == WL_OK && hflag)
+                rc = set_error(WL_ERR_ARG, "WL_LINKS_R8 needs SU(3) links (unitary, det 1, to 1e-6)");
+            if (rc != WL_OK) break;
+        }
         // the link build reads U: finish before returning so U may be freed
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(WL_ERR_CUDA, "link build failed"); break; }
     } while (0);
@@ -566,6 +637,7 @@ extern "C" int wl_gauge_destroy(wl_gauge g)
         for (int p = 0; p < 2; ++p) {
             if (g->links[prec][p]) cudaFree(g->links[prec][p]);
             if (g->links_r12[prec][p]) cudaFree(g->links_r12[prec][p]);
+            if (g->links_r8[prec][p]) cudaFree(g->links_r8[prec][p]);
         }
         if (g->tmp[prec]) cudaFree(g->tmp[prec]);
     }

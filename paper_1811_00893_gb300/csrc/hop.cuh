@@ -246,7 +246,8 @@ __device__ __forceinline__ void neighbours(const Geom& g, int p, int i, int (&nb
 // rebuilt as conj(row0 x row1) (unitarity with det = 1), and the phase is
 // applied to the projected half spinor of boundary-crossing hops.  Twelve
 // reals instead of eighteen per hop: 384 instead of 576 bytes per site in
-// FP32 (192 instead of 288 in FP16).
+// FP32 (192 instead of 288 in FP16).  LF = 2 (FP32, single-RHS launches): eight
+// reals per hop (load_link_r8), 256 bytes per site.
 // ---------------------------------------------------------------------------
 
 template <int P, int LF>
@@ -274,6 +275,10 @@ struct LinkLayout<WL_F32, 1> {  // per hop: 3 float4 = rows 0 and 1
 template <>
 struct LinkLayout<WL_F16, 1> {  // per hop: 1 uint4 (4 half2) + 1 uint2 (2 half2)
     static constexpr int n16 = 8, nsmall = 8, small_bytes = 8, bytes = 192;
+};
+template <>
+struct LinkLayout<WL_F32, 2> {  // per hop: 2 float4 (8 reals)
+    static constexpr int n16 = 16, nsmall = 0, small_bytes = 8, bytes = 256;
 };
 
 // row 2 = conj(row 0 x row 1)
@@ -316,6 +321,56 @@ __device__ __forceinline__ void load_link_r12<WL_F16>(cx<float> (&w)[9], const v
     w[4] = {f.x, f.y};
     w[5] = {h.x, h.y};
     su3_third_row(w);
+}
+
+// Eight reals per SU(3) matrix.  With rows (a, b, c) taken in the cyclic order
+// that puts the smaller of |W_00|, |W_10| first -- (W0, W1, W2), or (W1, W2, W0)
+// ("shifted") -- so that n = |a2|^2 + |a3|^2 = 1 - |a1|^2 >= 1/2, a hop stores
+// two planes of float4:
+//   (a2.re, a2.im, a3.re, a3.im), (b1.re, b1.im, t_a + 3 [shifted], t_c),
+// t_x = tan(arg(x1) / 4) in [-1, 1].  The rest follows from unitarity and
+// det = 1: |a1| = sqrt(1 - n); |c1| = sqrt(n - |b1|^2) (the first column is a
+// unit vector); b2, b3 solve the two linear equations (a, b) = 0 and
+// conj(c1) = a2 b3 - a3 b2 (row c is conj(a x b)), whose determinant is n;
+// then c2, c3 from c = conj(a x b).  The phases come back from t by the
+// tangent half-angle and double-angle formulas (rational: one reciprocal).
+// Elements near zero come back with ~sqrt of the FP32 rounding as absolute
+// error (a square root of a small difference); everything else to FP32
+// rounding.
+__device__ __forceinline__ cx<float> unit_from_tan4(float t)
+{
+    const float d = __frcp_rn(fmaf(t, t, 1.0f));
+    const float c = (1.0f - t * t) * d, s = 2.0f * t * d;  // cos, sin of 2 atan(t)
+    return {(c - s) * (c + s), 2.0f * s * c};
+}
+
+template <int P>
+__device__ __forceinline__ void load_link_r8(cx<float> (&w)[9], const void* base, long long Vh, int d,
+                                             long long i);
+template <>
+__device__ __forceinline__ void load_link_r8<WL_F32>(cx<float> (&w)[9], const void* base, long long Vh,
+                                                     int d, long long i)
+{
+    const float4* p = (const float4*)base + (long long)d * 2 * Vh;
+    const float4 q0 = p[i], q1 = p[Vh + i];
+    const bool shift = q1.z > 1.5f;  // t_a + 3 >= 2 when shifted, t_a <= 1 otherwise
+    const cx<float> a2 = {q0.x, q0.y}, a3 = {q0.z, q0.w}, b1 = {q1.x, q1.y};
+    const float n = fmaf(a2.re, a2.re, fmaf(a2.im, a2.im, fmaf(a3.re, a3.re, a3.im * a3.im)));
+    const float nb = fmaf(b1.re, b1.re, b1.im * b1.im);
+    const cx<float> a1 = sqrtf(fmaxf(0.0f, 1.0f - n)) * unit_from_tan4(shift ? q1.z - 3.0f : q1.z);
+    const cx<float> c1 = sqrtf(fmaxf(0.0f, n - nb)) * unit_from_tan4(q1.w);
+    const float inv = __frcp_rn(n);
+    const cx<float> ab = conj(a1) * b1;
+    const cx<float> b2 = (-inv) * (ab * a2 + conj(a3) * conj(c1));
+    const cx<float> b3 = inv * (conj(a2) * conj(c1) - ab * a3);
+    const cx<float> c2 = conj(a3 * b1 - a1 * b3), c3 = conj(a1 * b2 - a2 * b1);
+    const cx<float> ra[3] = {a1, a2, a3}, rb[3] = {b1, b2, b3}, rc[3] = {c1, c2, c3};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        w[k] = shift ? rc[k] : ra[k];
+        w[3 + k] = shift ? ra[k] : rb[k];
+        w[6 + k] = shift ? rb[k] : rc[k];
+    }
 }
 
 // FP16 spinor without its per-site norm applied (the caller scales the
@@ -518,7 +573,7 @@ __device__ __forceinline__ void hop_one(cx<typename Prec<P>::real> (&acc)[12], c
         for (int a = 0; a < 3; ++a)
             reconstruct_scaled<MU, S>(acc, a, dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h0),
                                       dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h1), nrm);
-    } else if constexpr (LF == 1) {
+    } else if constexpr (LF >= 1) {
         cx<T> h0[3], h1[3], W[9];
         load_project<P, MU, S>(h0, h1, in, Vh, nb);
         if (cross & (1u << D)) {  // boundary phase: phi forward, conj(phi) backward
@@ -529,7 +584,8 @@ __device__ __forceinline__ void hop_one(cx<typename Prec<P>::real> (&acc)[12], c
                 h1[c] = f * h1[c];
             }
         }
-        load_link_r12<P>(W, links, lVh, D, li);
+        if constexpr (LF == 1) load_link_r12<P>(W, links, lVh, D, li);
+        else load_link_r8<P>(W, links, lVh, D, li);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
             reconstruct<MU, S>(acc, a, dot3(W[3 * a], W[3 * a + 1], W[3 * a + 2], h0),
@@ -563,7 +619,7 @@ __device__ __forceinline__ void hop_apply(cx<typename Prec<P>::real> (&acc)[12],
                                           long long li, unsigned cross, const cx<float>* ph, float s = 1.0f)
 {
     using T = typename Prec<P>::real;
-    if constexpr (LF == 1) {
+    if constexpr (LF >= 1) {
         if (cross & (1u << D)) {
             const cx<T> f = (D & 1) ? conj(ph[MU]) : ph[MU];
 #pragma unroll
@@ -583,6 +639,7 @@ __device__ __forceinline__ void hop_apply(cx<typename Prec<P>::real> (&acc)[12],
     } else {
         cx<T> W[9];
         if constexpr (LF == 1) load_link_r12<P>(W, links, lVh, D, li);
+        else if constexpr (LF == 2) load_link_r8<P>(W, links, lVh, D, li);
         else load_link<P>(W, links, lVh, D, li);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {

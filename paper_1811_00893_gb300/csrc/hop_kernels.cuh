@@ -79,7 +79,7 @@ __device__ __forceinline__ void hop_kernel_site(const HopArgs& A, int rhs, int p
     cx<T> acc[12];
     int nb[8];
     unsigned cross = 0;
-    if constexpr (LF == 1) neighbours(A.g, A.parity0 + pidx, i, nb, cross);
+    if constexpr (LF >= 1) neighbours(A.g, A.parity0 + pidx, i, nb, cross);
     else neighbours(A.g, A.parity0 + pidx, i, nb);
     hop_site<P, DAG, LF>(acc, nb, A.g.Vh, A.in[pidx] + rhs * A.rs_in, A.links[pidx], A.g.Vh, i, cross,
                          A.ph);
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256, (MinBlocks<P, DOT>::value)) hop_mrhs_kern
     int nb[8];
     unsigned cross = 0;
     if (valid) {
-        if constexpr (LF == 1) neighbours(A.g, p, i, nb, cross);
+        if constexpr (LF >= 1) neighbours(A.g, p, i, nb, cross);
         else neighbours(A.g, p, i, nb);
     }
     for (int r = threadIdx.y; r < nrhs; r += blockDim.y) {
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(256, 2) hop_mrhs_pipe_kernel(const HopArgs A, 
         int nb[8];
         unsigned cross = 0;
         if (valid) {
-            if constexpr (LF == 1) neighbours(A.g, p, i, nb, cross);
+            if constexpr (LF >= 1) neighbours(A.g, p, i, nb, cross);
             else neighbours(A.g, p, i, nb);
         }
         for (int r = threadIdx.y; r < nrhs; r += blockDim.y) {
@@ -424,29 +424,38 @@ static const void* pipe_kernel_p(bool dagger, bool dot)
                : (const void*)hop_mrhs_pipe_kernel<P, false, false, CL, LF>;
 }
 
+// The eight-real link format (LF = 2) exists for FP32 single-RHS launches only.
 template <int CL, int LF>
 void HopKernels<CL, LF>::pipe(int prec, bool dagger, bool dot, const HopArgs& A, int nrhs, int ntiles,
                           dim3 grid, dim3 block, size_t smem, cudaStream_t s)
 {
-    if (prec == WL_F32) hop_pipe_p<CL, LF, WL_F32>(dagger, dot, A, nrhs, ntiles, grid, block, smem, s);
-    else hop_pipe_p<CL, LF, WL_F16>(dagger, dot, A, nrhs, ntiles, grid, block, smem, s);
+    if constexpr (LF < 2) {
+        if (prec == WL_F32) hop_pipe_p<CL, LF, WL_F32>(dagger, dot, A, nrhs, ntiles, grid, block, smem, s);
+        else hop_pipe_p<CL, LF, WL_F16>(dagger, dot, A, nrhs, ntiles, grid, block, smem, s);
+    }
 }
 
 template <int CL, int LF>
 const void* HopKernels<CL, LF>::pipe_kernel(int prec, bool dagger, bool dot)
 {
-    return prec == WL_F32 ? pipe_kernel_p<CL, LF, WL_F32>(dagger, dot) : pipe_kernel_p<CL, LF, WL_F16>(dagger, dot);
+    if constexpr (LF < 2)
+        return prec == WL_F32 ? pipe_kernel_p<CL, LF, WL_F32>(dagger, dot) : pipe_kernel_p<CL, LF, WL_F16>(dagger, dot);
+    return nullptr;
 }
 
 template <int CL, int LF>
 void HopKernels<CL, LF>::single(int prec, bool dagger, bool dot, const HopArgs& A, dim3 grid, int block,
                             cudaStream_t s)
 {
-    if (prec == WL_F32) hop_single_p<CL, LF, WL_F32>(dagger, dot, A, grid, block, s);
-    else if (prec == WL_F16) hop_single_p<CL, LF, WL_F16>(dagger, dot, A, grid, block, s);
-    else if constexpr (LF == 0) {
-        if (prec == WL_F64) hop_single_p<CL, LF, WL_F64>(dagger, dot, A, grid, block, s);
-        else hop_single_p<CL, LF, WL_DF64>(dagger, dot, A, grid, block, s);
+    if constexpr (LF == 2) {
+        if (prec == WL_F32) hop_single_p<CL, LF, WL_F32>(dagger, dot, A, grid, block, s);
+    } else {
+        if (prec == WL_F32) hop_single_p<CL, LF, WL_F32>(dagger, dot, A, grid, block, s);
+        else if (prec == WL_F16) hop_single_p<CL, LF, WL_F16>(dagger, dot, A, grid, block, s);
+        else if constexpr (LF == 0) {
+            if (prec == WL_F64) hop_single_p<CL, LF, WL_F64>(dagger, dot, A, grid, block, s);
+            else hop_single_p<CL, LF, WL_DF64>(dagger, dot, A, grid, block, s);
+        }
     }
 }
 
@@ -454,11 +463,13 @@ template <int CL, int LF>
 void HopKernels<CL, LF>::multi(int prec, bool dagger, bool dot, const HopArgs& A, int nrhs, dim3 grid,
                            dim3 block, size_t smem, cudaStream_t s)
 {
-    if (prec == WL_F32) hop_multi_p<CL, LF, WL_F32>(dagger, dot, A, nrhs, grid, block, smem, s);
-    else if (prec == WL_F16) hop_multi_p<CL, LF, WL_F16>(dagger, dot, A, nrhs, grid, block, smem, s);
-    else if constexpr (LF == 0) {
-        if (prec == WL_F64) hop_multi_p<CL, LF, WL_F64>(dagger, dot, A, nrhs, grid, block, smem, s);
-        else hop_multi_p<CL, LF, WL_DF64>(dagger, dot, A, nrhs, grid, block, smem, s);
+    if constexpr (LF < 2) {
+        if (prec == WL_F32) hop_multi_p<CL, LF, WL_F32>(dagger, dot, A, nrhs, grid, block, smem, s);
+        else if (prec == WL_F16) hop_multi_p<CL, LF, WL_F16>(dagger, dot, A, nrhs, grid, block, smem, s);
+        else if constexpr (LF == 0) {
+            if (prec == WL_F64) hop_multi_p<CL, LF, WL_F64>(dagger, dot, A, nrhs, grid, block, smem, s);
+            else hop_multi_p<CL, LF, WL_DF64>(dagger, dot, A, nrhs, grid, block, smem, s);
+        }
     }
 }
 
@@ -482,12 +493,14 @@ const void* HopKernels<CL, LF>::reducing(int prec, bool dagger)
 {
     if (prec == WL_F32)
         return dagger ? (const void*)hop_kernel<WL_F32, true, true, CL, LF> : (const void*)hop_kernel<WL_F32, false, true, CL, LF>;
-    if (prec == WL_F16)
-        return dagger ? (const void*)hop_kernel<WL_F16, true, true, CL, LF> : (const void*)hop_kernel<WL_F16, false, true, CL, LF>;
-    if constexpr (LF == 0) {
-        if (prec == WL_F64)
-            return dagger ? (const void*)hop_kernel<WL_F64, true, true, CL, LF> : (const void*)hop_kernel<WL_F64, false, true, CL, LF>;
-        return dagger ? (const void*)hop_kernel<WL_DF64, true, true, CL, LF> : (const void*)hop_kernel<WL_DF64, false, true, CL, LF>;
+    if constexpr (LF < 2) {
+        if (prec == WL_F16)
+            return dagger ? (const void*)hop_kernel<WL_F16, true, true, CL, LF> : (const void*)hop_kernel<WL_F16, false, true, CL, LF>;
+        if constexpr (LF == 0) {
+            if (prec == WL_F64)
+                return dagger ? (const void*)hop_kernel<WL_F64, true, true, CL, LF> : (const void*)hop_kernel<WL_F64, false, true, CL, LF>;
+            return dagger ? (const void*)hop_kernel<WL_DF64, true, true, CL, LF> : (const void*)hop_kernel<WL_DF64, false, true, CL, LF>;
+        }
     }
     return nullptr;
 }

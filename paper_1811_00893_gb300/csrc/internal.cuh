@@ -63,6 +63,7 @@ struct wl_gauge_s {
     void* links[4][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     // compressed (two-row) copies of the FP32 / FP16 links, when requested (WL_LINKS_R12)
     void* links_r12[4][2] = {};
+    void* links_r8[4][2] = {};  // eight-real links (FP32 only), see hop.cuh load_link_r8
     // grid-reduction scratch
     wl::RedScratch red = {nullptr, nullptr, 0};
     int red_slots = 0;

@@ -27,6 +27,7 @@ ERR_NAMES = {0: "WL_OK", -1: "WL_ERR_ARG", -2: "WL_ERR_CUDA", -3: "WL_ERR_NOT_CO
 
 #: wl_gauge_create flag: also keep two-row (reconstruct-12) FP32/FP16 links
 WL_LINKS_R12 = 1 << 8
+WL_LINKS_R8 = 1 << 9
 
 
 def prec_mask(*precs) -> int:
@@ -399,12 +400,12 @@ class Gauge:
     """Owns a wl_gauge handle; `fields(prec, nrhs)` allocates internal fields."""
 
     def __init__(self, dims, kappa, U: torch.Tensor, precs=("f64", "f32", "f16"),
-                 bc=(1, 1, 1, -1), stream=None, r12: bool = False):
+                 bc=(1, 1, 1, -1), stream=None, r12: bool = False, r8: bool = False):
         self.dims = tuple(int(d) for d in dims)
         self.kappa = float(kappa)
         self.bc = tuple(bc)
         self.lat = lattice(dims, kappa, bc)
-        mask = prec_mask(*precs) | (WL_LINKS_R12 if r12 else 0)
+        mask = prec_mask(*precs) | (WL_LINKS_R12 if r12 else 0) | (WL_LINKS_R8 if r8 else 0)
         self.handle = wl_gauge_create(self.lat, U, mask, stream)
         self.Vh = wl_half_volume(self.handle)
 

@@ -33,7 +33,7 @@ class Case:
     """A seeded lattice: canonical links on host and device, a gauge object."""
 
     def __init__(self, dims, kappa=0.12, kind="haar", seed=1, bc=(1, 1, 1, -1),
-                 precs=("f64", "f32", "f16"), device_gen=False, r12=False):
+                 precs=("f64", "f32", "f16"), device_gen=False, r12=False, r8=False):
         self.dims = tuple(dims)
         self.kappa = kappa
         self.bc = bc
@@ -41,7 +41,7 @@ class Case:
         U = fields.gauge_field(dims, kind, seed, device=dev)
         self.U_dev = U.to("cuda").contiguous()
         self.U = U.cpu().numpy()
-        self.g = wilson.Gauge(dims, kappa, self.U_dev, precs=precs, bc=bc, r12=r12)
+        self.g = wilson.Gauge(dims, kappa, self.U_dev, precs=precs, bc=bc, r12=r12, r8=r8)
         self.V = int(np.prod(dims))
         self.Vh = self.V // 2
 
