@@ -583,7 +583,8 @@ extern "C" int wl_dd_create_part(wl_dd* out, const wl_lattice* lat, const int* g
                 if (c[mu] == 0) edge |= 1u << (2 * mu + 1);
             }
             dd->edge[d] = edge;
-            rc = gauge_create(&dd->dom[d], &loc, lat, org, U, prec_mask, s);
+            // the decomposed kernels read full or twelve-real links only
+            rc = gauge_create(&dd->dom[d], &loc, lat, org, U, prec_mask & ~WL_LINKS_R8, s);
             if (rc == WL_OK) dd->dom[d]->dd_part = 1;
         }
         if (rc != WL_OK) break;
