@@ -371,12 +371,26 @@ int dd_launch_hop(wl_dd dd, const DDLaunch& h, cudaStream_t s)
     const int extra = (h.x1[0][0] ? 1 : 0) + (h.x2[0][0] ? 1 : 0) + (h.w[0][0] ? 1 : 0);
     const double site_bytes = (double)(lf ? (P == WL_F32 ? 384 : 192) : link_field_bytes(P, 1)) +
                               (h.cl_mode ? (double)clover_site_bytes(P) : 0.0) + (double)nrhs * (2 + extra) * sb;
+    // the interior of a y or z cut as a box (no site list to read)
+    bool box_ok = false;
+    {
+        long long nbox = g.Lxh;
+        for (int mu = 1; mu < 4; ++mu) {
+            const bool cut_mu = (dd->cut >> mu) & 1;
+            A.bo[mu] = cut_mu ? 1 : 0;
+            A.bn[mu] = cut_mu ? g.L[mu] - 2 : g.L[mu];
+            nbox *= A.bn[mu];
+        }
+        for (int k = 1; k <= 2; ++k) fast_div_magic(A.bn[k], &A.bm[k], &A.bsh[k]);
+        box_ok = nbox == dd->nint;
+    }
     // part 0: interior (one contiguous range when only t is cut), part 1: boundary
     auto run = [&](int part, DDArgs AA, cudaStream_t st_) -> int {
         const long long n = part ? dd->nbnd : dd->nint;
         if (n == 0) return WL_OK;
-        AA.sites = part ? dd->bsites : (t_only ? nullptr : dd->isites);
+        AA.sites = part ? dd->bsites : (t_only || box_ok ? nullptr : dd->isites);
         AA.site0 = (!part && t_only) ? g.st : 0;
+        AA.box = (!part && !t_only && box_ok) ? 1 : 0;
         AA.nsites = n;
         AA.nparity = np;
         AA.blocks_per_parity = part ? bb : bi;

@@ -178,8 +178,15 @@ struct DDArgs {
     long long hoff[2][4][2];
     int active_stride;
     const int* sites;      // the launch's sites: interior or boundary half indices, or
-    long long site0;       // (sites == nullptr) the contiguous range site0 .. site0 + nsites - 1
+    long long site0;       // (sites == nullptr, box == 0) the contiguous range site0 .. site0 + nsites - 1
     long long nsites;
+    // box == 1 (sites == nullptr): the interior as the box of sites with
+    // bo[mu] <= x_mu < bo[mu] + bn[mu] (mu = y, z, t; x whole), in half-index
+    // order; bm / bsh: round-up reciprocals of bn[1], bn[2]
+    int box;
+    int bo[4], bn[4];
+    unsigned bm[4];
+    int bsh[4];
     int blocks_per_parity;  // plain launches: one site per thread, a block's parity fixed
     int parity0, nparity;   // launches with a fused reduction loop over both parities' sites
     long long rs_in, rs_out, rs_x1, rs_x2, rs_w;

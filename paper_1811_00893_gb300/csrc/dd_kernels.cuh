@@ -15,6 +15,20 @@ namespace wl {
 
 static constexpr int kDDBlock = 128;
 
+// Half index of the j-th site of the interior box (the order of increasing
+// half index, as the site list it replaces).
+__device__ __forceinline__ int box_site(const DDArgs& A, long long j)
+{
+    const int q = (int)j;
+    const int r0 = geo_div(A.g, 0, q);  // j / Lxh
+    const int xh = q - r0 * A.g.Lxh;
+    const int r1 = A.bm[1] ? (int)(__umulhi((unsigned)r0, A.bm[1]) >> A.bsh[1]) : r0;
+    const int y = r0 - r1 * A.bn[1];
+    const int t = A.bm[2] ? (int)(__umulhi((unsigned)r1, A.bm[2]) >> A.bsh[2]) : r1;
+    const int z = r1 - t * A.bn[2];
+    return xh + A.g.Lxh * ((A.bo[1] + y) + A.g.L[1] * ((A.bo[2] + z) + A.g.L[2] * (A.bo[3] + t)));
+}
+
 // Output site j of the launch's site set, launch parity pidx: the hopping
 // term (halo reads on boundary sites) and the epilogue; with DOT its (w, out),
 // ||out||^2 are added to part.
@@ -23,7 +37,7 @@ __device__ __forceinline__ void dd_site(const DDArgs& A, const DDDom& D, int rhs
                                         typename Prec<P>::real (&part)[3])
 {
     using T = typename Prec<P>::real;
-    const int i = A.sites ? A.sites[j] : (int)(A.site0 + j);
+    const int i = A.sites ? A.sites[j] : A.box ? box_site(A, j) : (int)(A.site0 + j);
     const int p = A.parity0 + pidx;
     int c[4], xh, nb[8];
     half_coords(A.g, p, i, c, xh);

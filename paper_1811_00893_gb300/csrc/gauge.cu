@@ -32,19 +32,22 @@ Geom make_geom(const int* dims)
     // m = floor(2^(31+l) / d) + 1 < 2^32, floor(n m / 2^(31+l)) = n / d
     // exactly for 0 <= n < 2^31, since m d - 2^(31+l) <= d <= 2^l.
     const int div[3] = {g.Lxh, dims[1], dims[2]};
-    for (int k = 0; k < 3; ++k) {
-        const unsigned long long d = (unsigned long long)div[k];
-        if (d <= 1) {
-            g.dm[k] = 0;
-            g.ds[k] = 0;
-            continue;
-        }
-        int l = 0;
-        while ((1ull << l) < d) ++l;
-        g.dm[k] = (unsigned)((1ull << (31 + l)) / d + 1);
-        g.ds[k] = l - 1;
-    }
+    for (int k = 0; k < 3; ++k) fast_div_magic(div[k], &g.dm[k], &g.ds[k]);
     return g;
+}
+
+void fast_div_magic(int divisor, unsigned* m, int* shift)
+{
+    const unsigned long long d = (unsigned long long)divisor;
+    if (d <= 1) {  // m = 0 marks "divide by one"
+        *m = 0;
+        *shift = 0;
+        return;
+    }
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    *m = (unsigned)((1ull << (31 + l)) / d + 1);
+    *shift = l - 1;
 }
 
 bool is_capturing(cudaStream_t s)

@@ -185,6 +185,9 @@ int field_to_canonical(wl_gauge g, double* out, const void* in, int parity, int 
 // Blocks of `kernel` (block threads, dynamic smem bytes) that fit on the whole
 // GPU at once: the grid of a grid-stride kernel whose reduction should have
 // few partials.
+// Round-up reciprocal (m, shift) with floor(n m / 2^(32 + shift)) = n / divisor
+// for 0 <= n < 2^31 (m = 0: the divisor is 1); see make_geom.
+void fast_div_magic(int divisor, unsigned* m, int* shift);
 int resident_grid(const void* kernel, int block, size_t smem);
 
 // Second stage of a multi-slot reduction: one block per slot sums
