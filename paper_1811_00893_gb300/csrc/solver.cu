@@ -56,6 +56,9 @@ static void free_ws(Workspace* w)
     if (w->nrm_h) cudaFreeHost(w->nrm_h);
     if (w->graph) cudaGraphExecDestroy(w->graph);
     if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
+    if (w->aux) cudaStreamDestroy(w->aux);
+    if (w->ev_x) cudaEventDestroy(w->ev_x);
+    if (w->ev_sent) cudaEventDestroy(w->ev_sent);
 }
 
 }  // namespace wl
@@ -565,7 +568,7 @@ int residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
 // just formed as b_o + kappa H_oe x_e by the same FP64 operations.  With a
 // clover term x_o = A_oo^-1 (...) leaves a rounding-level odd residual, so
 // both halves are evaluated.
-int true_residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
+int true_residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s, double* dot_out)
 {
     const size_t hb = w->hb64;
     HopLaunch h;
@@ -590,7 +593,7 @@ int true_residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
     h.b1 = -1.0;
     h.a = g->kappa;
     h.dot = true;
-    h.dot_out = w->nrm;
+    h.dot_out = dot_out ? dot_out : w->nrm;
     return launch_hop(g, h, s);
 }
 
@@ -1044,8 +1047,13 @@ int SolveState::finalize(bool* retry_out)
         }
         WL_TRY(launch_hop(g, h, s));
     }
-    WL_TRY(true_residual64(g, w, nrhs, s));
-    WL_TRY(read_norms(w, nrhs, s));
+    WL_TRY(send_x());  // the caller's x is written while the check below runs
+    // the norms go straight to the pinned host buffer: a copy-engine read-back
+    // would queue behind the copy of x
+    double* nrm_dev = nullptr;
+    WL_CUDA(cudaHostGetDevicePointer((void**)&nrm_dev, w->nrm_h, 0));
+    WL_TRY(true_residual64(g, w, nrhs, s, nrm_dev));
+    WL_CUDA(cudaStreamSynchronize(s));
     bool retry = false, tighten = false;
     for (int k = 0; k < nrhs; ++k) {
         const double tr = bnorm2[k] > 0 ? std::sqrt(w->nrm_h[3 * k + 2] / bnorm2[k]) : 0.0;
@@ -1073,6 +1081,9 @@ int SolveState::finalize(bool* retry_out)
     true_resid.assign(rnorm2.begin(), rnorm2.end());
     *retry_out = retry;
     if (!retry) return WL_OK;
+    // the next rounds rewrite x: only after the side stream has read it
+    WL_CUDA(cudaStreamWaitEvent(s, w->ev_sent, 0));
+    x_sent = false;
     if (tighten) {  // the FP64 Schur residual met the goal but the full one did not: aim lower
         ++final_rounds;
         safety *= 0.1;
@@ -1085,12 +1096,37 @@ int SolveState::finalize(bool* retry_out)
     return WL_OK;
 }
 
-int SolveState::end(wl_solve_info* info)
+int SolveState::send_x()
 {
+    if (!w->aux) {
+        WL_CUDA(cudaStreamCreateWithFlags(&w->aux, cudaStreamNonBlocking));
+        WL_CUDA(cudaEventCreateWithFlags(&w->ev_x, cudaEventDisableTiming));
+        WL_CUDA(cudaEventCreateWithFlags(&w->ev_sent, cudaEventDisableTiming));
+    }
+    // the conversion runs on the solver's stream (the check that follows is a
+    // grid of resident blocks, which would hold it off the SMs); only the copy
+    // to the host, on the copy engine, runs beside the check
     const size_t hb64 = w->hb64;
     WL_TRY(field_to_canonical(g, xd, w->x64, 0, WL_F64, nrhs, s, 2 * (long long)hb64));
     WL_TRY(field_to_canonical(g, xd, (const char*)w->x64 + hb64, 1, WL_F64, nrhs, s, 2 * (long long)hb64));
-    if (host_x) WL_CUDA(cudaMemcpyAsync(x_user, xd, canon, cudaMemcpyDeviceToHost, s));
+    WL_CUDA(cudaEventRecord(w->ev_x, s));
+    WL_CUDA(cudaStreamWaitEvent(w->aux, w->ev_x, 0));
+    x_sent = true;  // from here on the side stream is waited for on every exit
+    if (host_x) WL_CUDA(cudaMemcpyAsync(x_user, xd, canon, cudaMemcpyDeviceToHost, w->aux));
+    WL_CUDA(cudaEventRecord(w->ev_sent, w->aux));
+    return WL_OK;
+}
+
+SolveState::~SolveState()
+{
+    // an early return must not leave a copy into the caller's buffer in flight
+    if (w && x_sent && w->aux) cudaStreamSynchronize(w->aux);
+}
+
+int SolveState::end(wl_solve_info* info)
+{
+    if (!x_sent) WL_TRY(send_x());
+    WL_CUDA(cudaStreamSynchronize(w->aux));
     WL_CUDA(cudaStreamSynchronize(s));
     const double secs =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -73,6 +73,9 @@ struct Workspace {
     bool graph_timed = false;   // captured while per-launch timing was on
     size_t graph_tslots = 0;    // its timed launches (capture slots)
     cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+    // the solution's canonical copy (and host copy) while the final check runs
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_x = nullptr, ev_sent = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -227,7 +230,9 @@ int run_chunk(wl_gauge g, Workspace* w, int nrhs, int k, bool use_graph, cudaStr
 void discount_chunk(wl_gauge g, Workspace* w, int skipped);
 int read_norms(Workspace* w, int nrhs, cudaStream_t s);
 int residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s);
-int true_residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s);
+// dot_out: where the norms go (default w->nrm; finalize passes the pinned
+// host buffer's device alias, so that no copy-engine transfer is needed)
+int true_residual64(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s, double* dot_out = nullptr);
 int inner_start(wl_gauge g, Workspace* w, int nrhs, const double* target2, double delta2,
                 cudaStream_t s);
 int reliable_update(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s);
@@ -283,6 +288,11 @@ struct SolveState {
     // reconstruct the odd half, the true residual of the full D; *retry asks
     // for more rounds with a tighter goal
     int finalize(bool* retry);
+    // write x to the caller's buffer on the side stream (x_sent): the canonical
+    // conversion and, for host x, the copy overlap the final check
+    int send_x();
+    bool x_sent = false;
+    ~SolveState();
     // x back to the caller's layout, per-rhs info; returns the first failure
     int end(wl_solve_info* info);
 };
