@@ -394,6 +394,15 @@ def test_clover_set_dd_errors_leave_no_term():
         with pytest.raises(wilson.WilsonError) as e:
             wilson.wl_clover_set(g, torch.from_numpy(F).cuda().contiguous())
         assert e.value.code == wilson.WL_ERR_STATE  # blocks take the term through the decomposition
+        # a valid term, then detached again: back to the Wilson operator
+        Fok = fields.clover_field(c.dims, 6).cuda().contiguous()
+        wilson.wl_dd_clover_set(c.dd.handle, Fok)
+        with_term = _mee_blocks(c, psi, "f64")
+        want_c = oracle.clover_Mee(c.U, Fok.cpu().numpy(), c.half(psi, 0), c.dims, c.bc, c.kappa)
+        assert rel(c.half(with_term, 0), want_c) <= TOL["f64"]
+        wilson.wl_dd_clover_set(c.dd.handle, None)
+        got = _mee_blocks(c, psi, "f64")
+        assert rel(c.half(got, 0), want) <= TOL["f64"]
     finally:
         c.close()
 

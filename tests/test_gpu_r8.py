@@ -68,6 +68,21 @@ def test_r8_D_and_Mee_match_oracle(case):
     assert rel(gotf[0].cpu().numpy(), wantf) < TOL["f32"]
 
 
+def test_r8_multi_rhs_launches_use_full_links(case):
+    """Multi-RHS launches on a gauge object with eight-real links take the
+    full links (the eight-real form is for single-RHS Wilson launches only)
+    and match the oracle."""
+    nrhs = 3
+    psi = case.source(nrhs=nrhs, seed=27)
+    inp = case.to_internal(psi, 1, "f32")
+    out = case.g.field("f32", nrhs)
+    wilson.wilson_dslash(case.g.handle, out, inp, 0, 0, wilson.WL_F32, nrhs)
+    got = case.to_canonical(out, 0, "f32", nrhs=nrhs)
+    for r in range(nrhs):
+        want = oracle.hop_eo(case.U, case.half(psi, 1, r), case.dims, case.bc, 0)
+        assert rel(case.half(got, 0, r), want) < TOL["f32"], r
+
+
 def test_r8_solve_reaches_true_residual(case):
     b = case.source(nrhs=1, seed=61)
     x = torch.zeros_like(b)
