@@ -261,10 +261,13 @@ int wilson_solve(wl_gauge g, double* x, const double* b, int nrhs, const wl_solv
 
 /* Solve nlat independent systems of different lattices together (the
  * batched form of wilson_solve): gauge object gs[l] with nrhs[l] right-hand
- * sides x[l], b[l] (device memory, canonical).  Each inner BiCGStab operator
+ * sides x[l], b[l] (canonical; device or host memory, host buffers staged
+ * through each gauge object's workspace).  Each inner BiCGStab operator
  * is one persistent hopping launch over 32-site tiles of all lattices (tiles
  * of lattices whose systems have all stopped are skipped), each vector update
- * one launch over all systems; the outer work runs per lattice.  Limits:
+ * one launch over all systems.  The outer work (set-up, FP64 residuals, final
+ * check, host copies) runs per lattice on each gauge object's own stream, so
+ * that the lattices' steps overlap; the call returns when all are done.  Limits:
  * 1 <= nlat <= 64, 1 <= nrhs[l] <= 32, even-odd systems only (p->eo = 1),
  * each gauge object at most once; WL_ERR_ARG otherwise.  A gauge object
  * with a clover term contributes D_clov.  info receives sum(nrhs) entries,

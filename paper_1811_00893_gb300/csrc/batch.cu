@@ -623,8 +623,17 @@ extern "C" int wilson_solve_batch(int nlat, const wl_gauge* gs, double* const* x
             if (gs[m] == gs[l]) return set_error(WL_ERR_ARG, "a gauge object appears twice in the batch");
     }
     cudaStream_t s = (cudaStream_t)stream;
+    // Each lattice's own work (set-up, FP64 residuals, final check) runs on its
+    // workspace's lane stream, so that the lattices' outer work overlaps on the
+    // GPU: every such step is issued for all lattices before the host waits
+    // for any of them.  The batched iterations run on s once every lane has
+    // been joined; the host waits for each chunk before the lanes go on.
     std::vector<SolveState> st(nlat);
-    for (int l = 0; l < nlat; ++l) WL_TRY(st[l].begin(gs[l], x[l], b[l], nrhs[l], prm, s));
+    for (int l = 0; l < nlat; ++l) WL_TRY(st[l].begin_issue(gs[l], x[l], b[l], nrhs[l], prm, s, true));
+    for (int l = 0; l < nlat; ++l) {
+        WL_CUDA(cudaStreamSynchronize(st[l].s));
+        st[l].begin_collect();
+    }
     std::shared_ptr<BatchCtx> ctx;
     WL_TRY(batch_context(st, prm->inner, &ctx));
     BatchCtx* C = ctx.get();
@@ -632,16 +641,39 @@ extern "C" int wilson_solve_batch(int nlat, const wl_gauge* gs, double* const* x
     std::vector<int> phase(nlat, PLAN);
     const int chunk = st[0].chunk;
     const bool use_graph = st[0].use_graph;
+    // end the round of every lattice in `ending` (its steps issued for all first)
+    auto end_rounds = [&](const std::vector<int>& ending) -> int {
+        std::vector<char> pending(nlat, 0);
+        for (int l : ending) {
+            bool p = false;
+            WL_TRY(st[l].finish_round_issue(&p));
+            pending[l] = p;
+        }
+        for (int l : ending) {
+            if (pending[l]) {
+                WL_CUDA(cudaStreamSynchronize(st[l].s));
+                st[l].finish_round_collect();
+            }
+            phase[l] = PLAN;
+        }
+        return WL_OK;
+    };
     for (;;) {
-        for (int l = 0; l < nlat; ++l) {
+        for (int l = 0; l < nlat; ++l)
             if (phase[l] == PLAN) {
                 bool any = false;
                 WL_TRY(st[l].plan(&any));
                 phase[l] = any ? ITER : FINAL;
             }
-            if (phase[l] == FINAL) {
+        {
+            std::vector<int> fin;
+            for (int l = 0; l < nlat; ++l)
+                if (phase[l] == FINAL) fin.push_back(l);
+            for (int l : fin) WL_TRY(st[l].finalize_issue());
+            for (int l : fin) {
+                WL_CUDA(cudaStreamSynchronize(st[l].s));
                 bool retry = false;
-                WL_TRY(st[l].finalize(&retry));
+                WL_TRY(st[l].finalize_collect(&retry));
                 phase[l] = retry ? PLAN : DONE;
             }
         }
@@ -662,29 +694,29 @@ extern "C" int wilson_solve_batch(int nlat, const wl_gauge* gs, double* const* x
             }
         if (wanted > 0) k = std::min(k, wanted);
         if (k <= 0) {  // a lattice ran out of iterations: end its round
+            std::vector<int> ending;
             for (int l = 0; l < nlat; ++l)
-                if (phase[l] == ITER && st[l].cap() <= 0) {
-                    WL_TRY(st[l].finish_round());
-                    phase[l] = PLAN;
-                }
+                if (phase[l] == ITER && st[l].cap() <= 0) ending.push_back(l);
+            WL_TRY(end_rounds(ending));
             continue;
         }
+        // the chunk reads every lattice's fields and scalars: after all lane work
+        for (int l = 0; l < nlat; ++l) WL_TRY(stream_join(s, st[l].s, st[l].w->ev_lane));
         if (C->lanes == 0) WL_TRY(tune_batch(*C, s));  // with the first round's systems active
         WL_TRY(run_batch_chunk(*C, k, use_graph && k == chunk, s));
         for (int l = 0; l < nlat; ++l)
             if (phase[l] == ITER)
                 WL_CUDA(cudaMemcpyAsync(st[l].w->sc_h, st[l].w->sc, sizeof(Scal) * st[l].nrhs,
                                         cudaMemcpyDeviceToHost, s));
-        WL_CUDA(cudaStreamSynchronize(s));
+        WL_CUDA(cudaStreamSynchronize(s));  // (the lanes' next work follows the chunk)
+        std::vector<int> ending;
         for (int l = 0; l < nlat; ++l) {
             if (phase[l] != ITER) continue;
             bool alive = false;
             WL_TRY(st[l].after_chunk(&alive));
-            if (!alive) {
-                WL_TRY(st[l].finish_round());
-                phase[l] = PLAN;
-            }
+            if (!alive) ending.push_back(l);
         }
+        WL_TRY(end_rounds(ending));
     }
     int rc = WL_OK, off = 0;
     for (int l = 0; l < nlat; ++l) {

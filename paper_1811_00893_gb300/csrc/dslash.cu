@@ -92,6 +92,11 @@ static const int kPipeShape = 16;
 static const int kFullGrid = 1000;
 // Single-RHS FP64 Wilson launches: three threads per site (hop_rows_kernel).
 static const int kRowsShape = 2000;
+// Multi-RHS launches of the wide types: kPerRhs + block size = the single-RHS
+// kernel with one grid row per right-hand side (grid.y), links read once per
+// right-hand side (these launches are bound by arithmetic, not by bytes);
+// reducing launches use the full grid and a finishing launch.
+static const int kPerRhs = 3000;
 
 static bool rows_allowed(const HopLaunch& h, int lf)
 {
@@ -137,6 +142,15 @@ static int launch_shape(const HopLaunch& h, int lf, HopArgs& A, int nrhs, int sh
         launch_single(h, lf, A, dim3(gx, 1), block, s);
         if (A.partials_only)
             return launch_finish_slots(A.red.partial, (long long)A.red.max_blocks * 3, (int)gx, 1,
+                                       A.dot_out, A.dot_stride, A.active, A.active_stride, s);
+    } else if (shape > kPerRhs) {
+        const int block = shape - kPerRhs;
+        A.blocks_per_parity = (int)((A.g.Vh + block - 1) / block);
+        gx = (unsigned)((long long)A.blocks_per_parity * h.nparity);
+        A.partials_only = h.dot ? 1 : 0;
+        launch_single(h, lf, A, dim3(gx, (unsigned)nrhs), block, s);
+        if (h.dot)
+            return launch_finish_slots(A.red.partial, (long long)A.red.max_blocks * 3, (int)gx, nrhs,
                                        A.dot_out, A.dot_stride, A.active, A.active_stride, s);
     } else if (shape > kPipeShape) {
         const dim3 block(kTile, shape - kPipeShape);
@@ -198,8 +212,10 @@ static int tuned_shape(wl_gauge g, const HopLaunch& h, int lf, HopArgs& A, int n
         const char* fs = getenv("WL_MRHS_SHAPE");
         const int v = fs ? atoi(fs) : 0;
         const bool narrow = h.prec == WL_F32 || h.prec == WL_F16;
+        const int pb = v - kPerRhs;
         if ((v >= 1 && v <= 8 && v <= nrhs) ||
-            (narrow && v > kPipeShape && v <= kPipeShape + 8 && v - kPipeShape <= nrhs)) {
+            (narrow && v > kPipeShape && v <= kPipeShape + 8 && v - kPipeShape <= nrhs) ||
+            pb == 64 || pb == 128 || pb == 256) {
             *shape = v;
             return WL_OK;
         }
@@ -209,15 +225,21 @@ static int tuned_shape(wl_gauge g, const HopLaunch& h, int lf, HopArgs& A, int n
     if (multi) {
         for (int l : {1, 2, 4, 8})
             if (l <= nrhs) cand.push_back(l);
-        if (h.prec == WL_F32 || h.prec == WL_F16)
+        if (h.prec == WL_F32 || h.prec == WL_F16) {
             for (int l : {2, 4, 8})
                 if (l <= nrhs) cand.push_back(kPipeShape + l);
+        } else {
+            for (int b : {64, 128, 256}) cand.push_back(kPerRhs + b);
+        }
     } else {
         cand = {64, 128, 256};
         if (h.dot)
             for (int b : {64, 128, 256}) cand.push_back(kFullGrid + b);
         if (rows_allowed(h, lf)) cand.push_back(kRowsShape);
     }
+    // the timings must not share the GPU with work on other streams (a
+    // batch's lattices run their own steps side by side)
+    WL_CUDA(cudaDeviceSynchronize());
     cudaEvent_t e0, e1;
     WL_CUDA(cudaEventCreate(&e0));
     WL_CUDA(cudaEventCreate(&e1));

@@ -59,6 +59,8 @@ static void free_ws(Workspace* w)
     if (w->aux) cudaStreamDestroy(w->aux);
     if (w->ev_x) cudaEventDestroy(w->ev_x);
     if (w->ev_sent) cudaEventDestroy(w->ev_sent);
+    if (w->lane) cudaStreamDestroy(w->lane);
+    if (w->ev_lane) cudaEventDestroy(w->ev_lane);
 }
 
 }  // namespace wl
@@ -275,10 +277,10 @@ int ensure_ws(wl_gauge g, int inner, int nrhs, int eo)
     }
     WL_TRY(ws_alloc((void**)&w->sc, sizeof(Scal) * n));
     WL_TRY(ws_alloc((void**)&w->mask, sizeof(int) * n));
-    WL_TRY(ws_alloc((void**)&w->nrm, sizeof(double) * 3 * n));
+    WL_TRY(ws_alloc((void**)&w->nrm, sizeof(double) * 6 * n));
     WL_CUDA(cudaMallocHost((void**)&w->sc_h, sizeof(Scal) * n));
     WL_CUDA(cudaMallocHost((void**)&w->mask_h, sizeof(int) * n));
-    WL_CUDA(cudaMallocHost((void**)&w->nrm_h, sizeof(double) * 3 * n));
+    WL_CUDA(cudaMallocHost((void**)&w->nrm_h, sizeof(double) * 6 * n));
     WL_CUDA(cudaMemset(w->sc, 0, sizeof(Scal) * n));
     std::memset(w->sc_h, 0, sizeof(Scal) * n);
     // reduction scratch for every kernel the solve launches (no growth later,
@@ -711,8 +713,24 @@ static int check_params(wl_gauge g, const void* x, const void* b, int nrhs,
     return WL_OK;
 }
 
+int stream_join(cudaStream_t into, cudaStream_t from, cudaEvent_t ev)
+{
+    WL_CUDA(cudaEventRecord(ev, from));
+    WL_CUDA(cudaStreamWaitEvent(into, ev, 0));
+    return WL_OK;
+}
+
 int SolveState::begin(wl_gauge g_, double* x, const double* b, int nrhs_, const wl_solve_params* p,
                       cudaStream_t s_)
+{
+    WL_TRY(begin_issue(g_, x, b, nrhs_, p, s_, false));
+    WL_CUDA(cudaStreamSynchronize(s));
+    begin_collect();
+    return WL_OK;
+}
+
+int SolveState::begin_issue(wl_gauge g_, double* x, const double* b, int nrhs_, const wl_solve_params* p,
+                            cudaStream_t s_, bool lane)
 {
     t0 = std::chrono::steady_clock::now();
     WL_TRY(check_params(g_, x, b, nrhs_, p));
@@ -726,6 +744,15 @@ int SolveState::begin(wl_gauge g_, double* x, const double* b, int nrhs_, const 
     WL_TRY(ensure_ws(g, P, nrhs, eo));
     w = g->ws;
     w->chunk_k = 0;
+    if (lane) {  // the workspace's own stream, after the caller's work on s
+        if (!w->lane) {
+            WL_CUDA(cudaStreamCreateWithFlags(&w->lane, cudaStreamNonBlocking));
+            WL_CUDA(cudaEventCreateWithFlags(&w->ev_lane, cudaEventDisableTiming));
+        }
+        WL_TRY(stream_join(w->lane, s_, w->ev_lane));
+        s = w->lane;
+        own_stream = true;
+    }
     const long long V = 2 * g->geo.Vh;
     canon = (size_t)V * 24 * sizeof(double) * nrhs;
 
@@ -762,15 +789,10 @@ int SolveState::begin(wl_gauge g_, double* x, const double* b, int nrhs_, const 
         WL_TRY(field_to_internal(g, (char*)w->xhi + hb64, xd, 1, w->outer, nrhs, s, 2 * (long long)hb64));
     }
     if (!prm->use_x0) WL_CUDA(cudaMemsetAsync(w->xhi, 0, 2 * hb64 * nrhs, s));
-    // ||b||^2 over the full lattice
-    WL_TRY(launch_cdot(g, WL_F64, w->b64, w->b64, 2, nrhs, w->nrm, 3, nullptr, s));
+    // ||b||^2 over the full lattice, into the second set of norm slots
+    WL_TRY(launch_cdot(g, WL_F64, w->b64, w->b64, 2, nrhs, w->nrm + 3 * nrhs, 3, nullptr, s));
     if (w->bout != w->b64)  // b in the outer precision
         WL_TRY(launch_convert(g, w->outer, w->bout, WL_F64, w->b64, 2, nrhs, nullptr, s));
-    WL_TRY(read_norms(w, nrhs, s));
-    bnorm2.assign(nrhs, 0.0);
-    rnorm2.assign(nrhs, 0.0);
-    target2.assign(nrhs, 0.0);
-    for (int k = 0; k < nrhs; ++k) bnorm2[k] = w->nrm_h[3 * k + 2];
     // b' = b_e + kappa H_eo b_o (even-odd) or b (full)
     if (eo) {
         HopLaunch h;
@@ -793,6 +815,27 @@ int SolveState::begin(wl_gauge g_, double* x, const double* b, int nrhs_, const 
     } else {
         WL_CUDA(cudaMemcpyAsync(w->bp, w->bout, 2 * hb64 * nrhs, cudaMemcpyDeviceToDevice, s));
     }
+    for (int k = 0; k < nrhs; ++k) std::memset(&w->sc_h[k], 0, sizeof(Scal));
+    WL_CUDA(cudaMemcpyAsync(w->sc, w->sc_h, sizeof(Scal) * nrhs, cudaMemcpyHostToDevice, s));
+    // the first residual of every right-hand side (a zero b is found by the
+    // host afterwards and never iterated)
+    for (int k = 0; k < nrhs; ++k) w->mask_h[k] = 1;
+    if (prm->use_x0) {
+        WL_TRY(upload_mask(w, nrhs, s));
+        WL_TRY(residual64(g, w, nrhs, s));
+    } else {  // x = 0: r = b' exactly, no FP64 matrix apply needed
+        WL_CUDA(cudaMemcpyAsync(w->rhi, w->bp, w->vb64 * nrhs, cudaMemcpyDeviceToDevice, s));
+        WL_TRY(launch_cdot(g, w->outer, w->bp, w->bp, w->nhalf, nrhs, w->nrm, 3, nullptr, s));
+    }
+    WL_CUDA(cudaMemcpyAsync(w->nrm_h, w->nrm, sizeof(double) * 6 * nrhs, cudaMemcpyDeviceToHost, s));
+    return WL_OK;
+}
+
+void SolveState::begin_collect()
+{
+    bnorm2.assign(nrhs, 0.0);
+    rnorm2.assign(nrhs, 0.0);
+    target2.assign(nrhs, 0.0);
     done.assign(nrhs, 0);
     final_target.assign(nrhs, 0);
     shortcut.assign(nrhs, 0);
@@ -804,21 +847,10 @@ int SolveState::begin(wl_gauge g_, double* x, const double* b, int nrhs_, const 
     poisoned.assign(nrhs, 0);
     iters_before.assign(nrhs, 0);
     for (int k = 0; k < nrhs; ++k) {
+        bnorm2[k] = w->nrm_h[3 * nrhs + 3 * k + 2];
         if (bnorm2[k] == 0.0) done[k] = 1;  // x = 0 solves b = 0 exactly
-        std::memset(&w->sc_h[k], 0, sizeof(Scal));
+        rnorm2[k] = done[k] ? 0.0 : w->nrm_h[3 * k + 2];
     }
-    WL_CUDA(cudaMemcpyAsync(w->sc, w->sc_h, sizeof(Scal) * nrhs, cudaMemcpyHostToDevice, s));
-    for (int k = 0; k < nrhs; ++k) w->mask_h[k] = done[k] ? 0 : 1;
-    WL_TRY(upload_mask(w, nrhs, s));
-    if (prm->use_x0) {
-        WL_TRY(residual64(g, w, nrhs, s));
-    } else {  // x = 0: r = b' exactly, no FP64 matrix apply needed
-        WL_CUDA(cudaMemcpyAsync(w->rhi, w->bp, w->vb64 * nrhs, cudaMemcpyDeviceToDevice, s));
-        WL_TRY(launch_cdot(g, w->outer, w->bp, w->bp, w->nhalf, nrhs, w->nrm, 3, w->mask, s));
-    }
-    WL_TRY(read_norms(w, nrhs, s));
-    for (int k = 0; k < nrhs; ++k) rnorm2[k] = w->mask_h[k] ? w->nrm_h[3 * k + 2] : 0.0;
-
     delta2 = prm->delta > 0.0 ? prm->delta * prm->delta : 0.0;
     // default inner reduction per round: FP32 to 3e-6 (a sweep over 1e-4 .. 3e-7
     // on the 32^3 x 64, 12-RHS and clover workloads found it fastest), FP16 to 1e-3
@@ -828,7 +860,6 @@ int SolveState::begin(wl_gauge g_, double* x, const double* b, int nrhs_, const 
     use_graph = prm->graph_iters >= 0;
     safety = 0.5;  // aim below tol on the Schur residual; tightened if the true residual misses
     final_rounds = 0;
-    return WL_OK;
 }
 
 int SolveState::plan(bool* any_out)
@@ -970,6 +1001,17 @@ int SolveState::after_chunk(bool* alive)
 
 int SolveState::finish_round()
 {
+    bool pending = false;
+    WL_TRY(finish_round_issue(&pending));
+    if (!pending) return WL_OK;
+    WL_CUDA(cudaStreamSynchronize(s));
+    finish_round_collect();
+    return WL_OK;
+}
+
+int SolveState::finish_round_issue(bool* pending)
+{
+    *pending = false;
     const int nh = w->nhalf;
     int any_poison = 0;
     for (int k = 0; k < nrhs; ++k) {
@@ -1006,7 +1048,13 @@ int SolveState::finish_round()
     if (!need) return WL_OK;
     WL_TRY(upload_mask(w, nrhs, s));
     WL_TRY(residual64(g, w, nrhs, s));
-    WL_TRY(read_norms(w, nrhs, s));
+    WL_CUDA(cudaMemcpyAsync(w->nrm_h, w->nrm, sizeof(double) * 3 * nrhs, cudaMemcpyDeviceToHost, s));
+    *pending = true;
+    return WL_OK;
+}
+
+void SolveState::finish_round_collect()
+{
     for (int k = 0; k < nrhs; ++k)
         if (part[k]) {
             rnorm2[k] = w->nrm_h[3 * k + 2];
@@ -1022,10 +1070,16 @@ int SolveState::finish_round()
                 status[k] = WL_ERR_NOT_CONVERGED;
             }
         }
-    return WL_OK;
 }
 
 int SolveState::finalize(bool* retry_out)
+{
+    WL_TRY(finalize_issue());
+    WL_CUDA(cudaStreamSynchronize(s));
+    return finalize_collect(retry_out);
+}
+
+int SolveState::finalize_issue()
 {
     const size_t hb64 = w->hb64;
     if (w->x64 != w->xhi)  // the solution in FP64 (the even half for even-odd solves)
@@ -1052,8 +1106,11 @@ int SolveState::finalize(bool* retry_out)
     // would queue behind the copy of x
     double* nrm_dev = nullptr;
     WL_CUDA(cudaHostGetDevicePointer((void**)&nrm_dev, w->nrm_h, 0));
-    WL_TRY(true_residual64(g, w, nrhs, s, nrm_dev));
-    WL_CUDA(cudaStreamSynchronize(s));
+    return true_residual64(g, w, nrhs, s, nrm_dev);
+}
+
+int SolveState::finalize_collect(bool* retry_out)
+{
     bool retry = false, tighten = false;
     for (int k = 0; k < nrhs; ++k) {
         const double tr = bnorm2[k] > 0 ? std::sqrt(w->nrm_h[3 * k + 2] / bnorm2[k]) : 0.0;
@@ -1120,7 +1177,9 @@ int SolveState::send_x()
 SolveState::~SolveState()
 {
     // an early return must not leave a copy into the caller's buffer in flight
+    // (nor, on a lane stream, work that reads or writes the caller's buffers)
     if (w && x_sent && w->aux) cudaStreamSynchronize(w->aux);
+    if (own_stream && s) cudaStreamSynchronize(s);
 }
 
 int SolveState::end(wl_solve_info* info)

@@ -57,7 +57,7 @@ struct Workspace {
     Scal* sc_h = nullptr;  // pinned
     int* mask = nullptr;
     int* mask_h = nullptr;  // pinned
-    double* nrm = nullptr;  // 3 doubles per rhs
+    double* nrm = nullptr;  // 6 doubles per rhs: two sets of 3 (dot, norm)
     double* nrm_h = nullptr;  // pinned
     // staging of host buffers
     double* stage_b = nullptr;
@@ -76,7 +76,13 @@ struct Workspace {
     // the solution's canonical copy (and host copy) while the final check runs
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_x = nullptr, ev_sent = nullptr;
+    // this gauge object's own stream, for its share of a batch's per-lattice work
+    cudaStream_t lane = nullptr;
+    cudaEvent_t ev_lane = nullptr;
 };
+
+// Make `into` wait for the work already enqueued on `from` (ev: a scratch event).
+int stream_join(cudaStream_t into, cudaStream_t from, cudaEvent_t ev);
 
 // ---------------------------------------------------------------------------
 // per-site BiCGStab updates (device), used by single and batched kernels
@@ -248,6 +254,7 @@ struct SolveState {
     const wl_solve_params* prm = nullptr;
     int nrhs = 0, eo = 0, P = 0;
     cudaStream_t s = nullptr;
+    bool own_stream = false;  // s is the workspace's lane stream (batched solves)
     double* x_user = nullptr;
     double* xd = nullptr;
     bool host_x = false;
@@ -265,9 +272,19 @@ struct SolveState {
     bool use_graph = false;
     std::chrono::steady_clock::time_point t0;
 
-    // set up: stage host buffers, convert b (and x0), b', norms, r = b' - A x0
+    // The steps that need host values computed on the device come in two
+    // halves: *_issue enqueues the work and the read-back, *_collect uses the
+    // values once the caller has synchronised s.  A batch issues every
+    // lattice's half on its own stream before it waits for any of them.
+
+    // set up: stage host buffers, convert b (and x0), b', ||b||^2, r = b' - A x0
+    // and ||r||^2.  With lane, the work runs on the workspace's own stream,
+    // after the work already on s.
     int begin(wl_gauge g, double* x, const double* b, int nrhs, const wl_solve_params* p,
               cudaStream_t s);
+    int begin_issue(wl_gauge g, double* x, const double* b, int nrhs, const wl_solve_params* p,
+                    cudaStream_t s, bool lane);
+    void begin_collect();
     // choose the right-hand sides of the next inner round and start it; *any
     // is false when no right-hand side needs one
     int plan(bool* any);
@@ -283,11 +300,16 @@ struct SolveState {
     // after a chunk: reliable updates, breakdowns, iteration limits; *alive is
     // false once every right-hand side of the round has stopped
     int after_chunk(bool* alive);
-    // end a round: x += x_lo in FP64 and the FP64 residual
+    // end a round: x += x_lo in FP64 and the FP64 residual (*pending: a
+    // read-back was issued and collect must follow the synchronisation)
     int finish_round();
+    int finish_round_issue(bool* pending);
+    void finish_round_collect();
     // reconstruct the odd half, the true residual of the full D; *retry asks
     // for more rounds with a tighter goal
     int finalize(bool* retry);
+    int finalize_issue();
+    int finalize_collect(bool* retry);
     // write x to the caller's buffer on the side stream (x_sent): the canonical
     // conversion and, for host x, the copy overlap the final check
     int send_x();

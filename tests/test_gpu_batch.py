@@ -120,3 +120,29 @@ def test_alternating_batches_keep_their_contexts():
     finally:
         for c in cases:
             c.close()
+
+
+def test_batch_with_host_buffers_on_a_busy_stream():
+    """Host and device buffers mixed in one batch (pinned host, pageable host,
+    device), called on a side stream whose last work, the write of a device b,
+    is still running when the call starts: every lattice's own stream waits for
+    the caller's stream, and every solve reaches the oracle residual."""
+    cases, bs = make_batch(SMALL)
+    try:
+        nr = [b.shape[0] for b in bs]
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            b0 = torch.empty_like(bs[0])
+            torch.cuda._sleep(50_000_000)  # about 25 ms of GPU time before b0 is written
+            b0.copy_(bs[0])
+        bb = [b0, bs[1].cpu().pin_memory(), bs[2].cpu(), bs[3]]
+        xs = [torch.zeros_like(bs[0]), torch.zeros_like(bb[1]).pin_memory(), torch.zeros_like(bb[2]),
+              torch.zeros_like(bs[3])]
+        p = wilson.solve_params(tol=TOL, eo=True, inner=wilson.WL_F32, graph_iters=4)
+        rc, infos = wilson.wilson_solve_batch([c.g.handle for c in cases], xs, bb, nr, p, stream=side)
+        side.synchronize()
+        check(cases, bs, xs, infos)
+    finally:
+        for c in cases:
+            c.close()

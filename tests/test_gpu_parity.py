@@ -203,12 +203,13 @@ def test_cdot_matches_oracle(case, prec):
     assert torch.equal(out, out2)
 
 
-@pytest.mark.parametrize("shape", [1, 3, 18, 20, 21])
+@pytest.mark.parametrize("shape", [1, 3, 18, 20, 21, 3064, 3256])
 @pytest.mark.parametrize("prec", ["f32", "f16"])
 def test_multi_rhs_shapes_match_oracle(monkeypatch, prec, shape):
     """Every multi-RHS launch shape the autotuner may pick (warps per block of
-    the staged kernel; 16 + warps for the pipelined persistent kernel) gives
-    the oracle's hopping term and reductions, on a lattice whose last 32-site
+    the staged kernel; 16 + warps for the pipelined persistent kernel; 3000 +
+    block size for one single-RHS grid row per right-hand side) gives the
+    oracle's hopping term and reductions, on a lattice whose last 32-site
     tile is half empty (Vh = 144).  The solve also runs its FP64 and
     double-float multi-RHS launches in the forced shape."""
     monkeypatch.setenv("WL_MRHS_SHAPE", str(shape))
@@ -232,6 +233,30 @@ def test_multi_rhs_shapes_match_oracle(monkeypatch, prec, shape):
         bn, xn = b.cpu().numpy(), x.cpu().numpy()
         for r in range(nrhs):
             assert oracle.true_residual(c.U, bn[r], xn[r], c.dims, c.bc, c.kappa) <= 1e-10
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("shape", [2, 3064, 3128, 3256])
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+def test_wide_multi_rhs_shapes_match_oracle(monkeypatch, prec, shape):
+    """The FP64 and double-float multi-RHS hopping term in the staged kernel
+    and in one single-RHS grid row per right-hand side (the shapes the
+    autotuner chooses among for the wide types) equals the oracle's, with and
+    without dagger, on a lattice with a ragged last tile and a twisted phase."""
+    monkeypatch.setenv("WL_MRHS_SHAPE", str(shape))
+    c = Case((6, 4, 2, 6), kappa=0.124, kind="haar", seed=9, bc=(1, np.exp(0.3j), 1, -1))
+    try:
+        nrhs = 3
+        psi = c.source(nrhs=nrhs, seed=73)
+        for dagger in (0, 1):
+            inp = c.to_internal(psi, 1, prec)
+            out = c.g.field(prec, nrhs)
+            wilson.wilson_dslash(c.g.handle, out, inp, 0, dagger, PRECS[prec], nrhs)
+            got = c.to_canonical(out, 0, prec, nrhs=nrhs)
+            for r in range(nrhs):
+                want = oracle.hop_eo(c.U, c.half(psi, 1, r), c.dims, c.bc, 0, dagger=bool(dagger))
+                assert rel(c.half(got, 0, r), want) < TOL[prec], (shape, dagger, r)
     finally:
         c.close()
 
