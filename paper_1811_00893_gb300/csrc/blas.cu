@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -73,7 +74,10 @@ __device__ __forceinline__ const char* at(const void* base, const Vec& v, int rh
     return (const char*)base + rhs * v.rstride + h * v.hb;
 }
 
-template <int P>
+// (a, b) and ||b||^2 per right-hand side.  NORM: a is b, and only the norm
+// is formed ((b, b) is that norm, with a zero imaginary part); for the FP64
+// fields that is a third of the FP64 arithmetic.
+template <int P, bool NORM>
 __global__ void __launch_bounds__(256) cdot_kernel(const void* a, const void* b, Vec v, double* out,
                                                    int out_stride, const int* mask, RedScratch red)
 {
@@ -85,14 +89,20 @@ __global__ void __launch_bounds__(256) cdot_kernel(const void* a, const void* b,
          j += (long long)gridDim.x * blockDim.x) {
         long long i;
         cx<T> x[12], y[12];
-        load_spinor<P>(x, at(a, v, rhs, j, i), v.Vh, i);
         load_spinor<P>(y, at(b, v, rhs, j, i), v.Vh, i);
         T cr = 0, ci = 0, nn = 0;
+        if (NORM) {
 #pragma unroll
-        for (int c = 0; c < 12; ++c) {
-            cr = fma(x[c].re, y[c].re, fma(x[c].im, y[c].im, cr));
-            ci = fma(x[c].re, y[c].im, fma(-x[c].im, y[c].re, ci));
-            nn = fma(y[c].re, y[c].re, fma(y[c].im, y[c].im, nn));
+            for (int c = 0; c < 12; ++c) nn = fma(y[c].re, y[c].re, fma(y[c].im, y[c].im, nn));
+            cr = nn;
+        } else {
+            load_spinor<P>(x, at(a, v, rhs, j, i), v.Vh, i);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                cr = fma(x[c].re, y[c].re, fma(x[c].im, y[c].im, cr));
+                ci = fma(x[c].re, y[c].im, fma(-x[c].im, y[c].re, ci));
+                nn = fma(y[c].re, y[c].re, fma(y[c].im, y[c].im, nn));
+            }
         }
         part[0] += (double)cr;
         part[1] += (double)ci;
@@ -181,18 +191,24 @@ int launch_cdot(wl_gauge g, int prec, const void* a, const void* b, int nhalf, i
                 double* out, int out_stride, const int* mask, cudaStream_t s, long long rs)
 {
     dim3 grid = blas_grid(g, nhalf, nrhs);
-    const void* kern = prec == WL_F64 ? (const void*)cdot_kernel<WL_F64>
-                       : prec == WL_F32 ? (const void*)cdot_kernel<WL_F32>
-                       : prec == WL_F16 ? (const void*)cdot_kernel<WL_F16>
-                                        : (const void*)cdot_kernel<WL_DF64>;
+    const bool norm = a == b;
+    const void* kern = prec == WL_F64 ? (const void*)cdot_kernel<WL_F64, false>
+                       : prec == WL_F32 ? (const void*)cdot_kernel<WL_F32, false>
+                       : prec == WL_F16 ? (const void*)cdot_kernel<WL_F16, false>
+                                        : (const void*)cdot_kernel<WL_DF64, false>;
     grid.x = std::min(grid.x, (unsigned)resident_grid(kern, kBlasBlock, 0));
     WL_TRY(ensure_red(g, nrhs, grid.x));
     const Vec v = make_vec(g, prec, nhalf, rs);
-    if (prec == WL_F64) cdot_kernel<WL_F64><<<grid, kBlasBlock, 0, s>>>(a, b, v, out, out_stride, mask, g->red);
-    else if (prec == WL_F32) cdot_kernel<WL_F32><<<grid, kBlasBlock, 0, s>>>(a, b, v, out, out_stride, mask, g->red);
-    else if (prec == WL_F16) cdot_kernel<WL_F16><<<grid, kBlasBlock, 0, s>>>(a, b, v, out, out_stride, mask, g->red);
-    else cdot_kernel<WL_DF64><<<grid, kBlasBlock, 0, s>>>(a, b, v, out, out_stride, mask, g->red);
-    WL_CHECK_LAUNCH(2.0 * v.hb * nhalf * nrhs);
+    auto go = [&](auto nt) {
+        constexpr bool N = decltype(nt)::value;
+        if (prec == WL_F64) cdot_kernel<WL_F64, N><<<grid, kBlasBlock, 0, s>>>(a, b, v, out, out_stride, mask, g->red);
+        else if (prec == WL_F32) cdot_kernel<WL_F32, N><<<grid, kBlasBlock, 0, s>>>(a, b, v, out, out_stride, mask, g->red);
+        else if (prec == WL_F16) cdot_kernel<WL_F16, N><<<grid, kBlasBlock, 0, s>>>(a, b, v, out, out_stride, mask, g->red);
+        else cdot_kernel<WL_DF64, N><<<grid, kBlasBlock, 0, s>>>(a, b, v, out, out_stride, mask, g->red);
+    };
+    if (norm) go(std::true_type{});
+    else go(std::false_type{});
+    WL_CHECK_LAUNCH((norm ? 1.0 : 2.0) * v.hb * nhalf * nrhs);
     return WL_OK;
 }
 

@@ -24,6 +24,29 @@ namespace wl {
 __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
 
+// Conversions between binary64 and binary32 by integer operations on the
+// IEEE 754 encodings.  GB300 runs the FP64 pipe, and with it the hardware
+// conversions between the two formats, at a small fraction of the integer
+// rate, so the conversion of whole fields between FP64 and df64 is done here
+// from the formats' definitions; values outside the common range take the
+// hardware conversions.  Both give the same bits.
+
+// binary32 -> binary64, exact: a normal float's biased exponent e (bias 127)
+// becomes e + 896 (bias 1023) and its 23 fraction bits the top of the 52;
+// zeros keep their sign.  Subnormals, infinities and NaNs: hardware.
+__device__ __forceinline__ double widen_f32(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned mag = u & 0x7fffffffu;
+    if ((mag >> 23) - 1u >= 254u) {  // biased exponent 0 or 255
+        if (mag == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
+        return (double)f;
+    }
+    const unsigned long long bits =
+        ((unsigned long long)(u & 0x80000000u) << 32) | (((unsigned long long)mag << 29) + (896ull << 52));
+    return __longlong_as_double((long long)bits);
+}
+
 struct df64 {
     float hi, lo;
 
@@ -31,13 +54,37 @@ struct df64 {
     __host__ __device__ df64(float h, float l) : hi(h), lo(l) {}
     __device__ df64(int v) : hi((float)v), lo(0.f) {}
     __device__ df64(float v) : hi(v), lo(0.f) {}
-    // nearest df64 to an FP64 value: hi = fl32(v), lo = fl32(v - hi)
+    // nearest df64 to an FP64 value: hi = RN32(v), lo = RN32(v - hi), where
+    // v - hi is exact in binary64.  For zeros and for biased exponents E in
+    // [949, 1149] (2^-74 <= |v| < 2^127) from the encoding: hi is v's 53-bit
+    // significand rounded to 24 bits, ties to even, a carry running into the
+    // exponent field as the format provides; v - hi is the signed remainder r
+    // of that rounding (|r| <= 2^28) times 2^(E-1075), whose nearest float is
+    // RN32(r) 2^(E-1075) -- the scaling by a power of two is exact because the
+    // product stays a normal float for every nonzero r in this range.
     __device__ df64(double v)
     {
-        hi = __double2float_rn(v);
-        lo = __double2float_rn(v - (double)hi);
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        const unsigned E = (unsigned)(b >> 52) & 0x7ffu;
+        const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+        if (E - 949u > 200u) {
+            if ((b << 1) == 0ull) {  // +-0: hi keeps the sign, lo = v - hi = +0
+                hi = __uint_as_float(sign);
+                lo = 0.f;
+            } else {
+                hi = __double2float_rn(v);
+                lo = __double2float_rn(v - (double)hi);
+            }
+            return;
+        }
+        const unsigned low = (unsigned)b & 0x1fffffffu;       // the 29 fraction bits rounded off
+        const unsigned up = (unsigned)(b >> 29) & 0x7fffffu;  // the 23 kept
+        const unsigned rnd = (low > 0x10000000u || (low == 0x10000000u && (up & 1u))) ? 1u : 0u;
+        hi = __uint_as_float(sign | ((((E - 896u) << 23) | up) + rnd));
+        const int r = (int)low - (int)(rnd << 29);  // |v| - |hi| in units of 2^(E-1075)
+        lo = __int2float_rn(sign ? -r : r) * __uint_as_float((E - 948u) << 23);
     }
-    __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __device__ explicit operator double() const { return widen_f32(hi) + widen_f32(lo); }
     __device__ explicit operator float() const { return __fadd_rn(hi, lo); }
 };
 

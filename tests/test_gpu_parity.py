@@ -77,6 +77,54 @@ def test_conversion_round_trip(case, prec):
             assert err < {"f32": 1e-7, "f16": 1.3e-3, "df64": 1e-14}[prec], err
 
 
+def _df64_test_values(n, rng):
+    """Doubles over the whole binary32 range, with the edge cases of the
+    double-float split: both ends of its integer-arithmetic range (biased
+    exponents 949 and 1149) and the exponents just outside, exact ties of the
+    24-bit rounding with an odd and an even kept bit, carries into the
+    exponent, signed zeros, binary32 subnormals and values below them."""
+    e = rng.integers(1023 - 152, 1023 + 128, n).astype(np.uint64)  # biased exponents
+    frac = rng.integers(0, 1 << 52, n, dtype=np.uint64)
+    sign = rng.integers(0, 2, n).astype(np.uint64) << np.uint64(63)
+    k = n // 8
+    e[:k] = rng.choice([947, 948, 949, 950, 1148, 1149, 1150], k).astype(np.uint64)
+    half = np.uint64(1 << 28)
+    kept = rng.integers(0, 1 << 23, 2 * k, dtype=np.uint64) << np.uint64(29)
+    frac[k:3 * k] = kept | half  # ties: kept bit odd or even
+    frac[3 * k:3 * k + 8] = np.uint64((1 << 52) - 1)  # rounds up into the exponent
+    e[3 * k + 4:3 * k + 8] = 1149
+    bits = sign | (e << np.uint64(52)) | frac
+    bits[-4:] = [0, 1 << 63, 0, 1 << 63]  # signed zeros
+    return bits.view(np.float64)
+
+
+def test_df64_conversion_bits():
+    """FP64 -> df64 -> FP64 through the layout conversions is, bit for bit,
+    hi = RN32(v), lo = RN32(v - hi) and hi + lo with numpy's IEEE 754
+    conversions and sum (for these values hi + lo is exact in binary64 or
+    rounds the same way on both sides), on every component of both parities."""
+    c = Case((4, 2, 2, 4), kappa=0.12, kind="haar", seed=3)
+    try:
+        rng = np.random.default_rng(17)
+        v = _df64_test_values(c.V * 24, rng)
+        psi = torch.from_numpy(v.copy()).view(torch.complex128).reshape(1, c.V, 4, 3).cuda()
+        back = torch.zeros_like(psi)
+        odd = torch.from_numpy(np.indices(c.dims[::-1]).sum(0).reshape(-1) % 2 == 1).cuda()
+        for p in (0, 1):
+            internal = c.to_internal(psi, p, "df64")
+            part = c.to_canonical(internal, p, "df64", nrhs=1)
+            sites = odd if p else ~odd
+            back[:, sites] = part[:, sites]  # (a copy keeps the sign of zeros)
+        hi = v.astype(np.float32)
+        lo = (v - hi.astype(np.float64)).astype(np.float32)
+        want = hi.astype(np.float64) + lo.astype(np.float64)
+        got = torch.view_as_real(back).reshape(-1).cpu().numpy()
+        bad = np.nonzero(got.view(np.uint64) != want.view(np.uint64))[0]
+        assert bad.size == 0, [(v[j], got[j], want[j]) for j in bad[:5]]
+    finally:
+        c.close()
+
+
 def test_f16_spinor_codec_error_bound(case):
     """Each component of a stored WL_F16 spinor is within the rounding of the
     build's 16-bit encoding (wl_spinor16_format) of the exact value.  With m the
