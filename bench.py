@@ -470,8 +470,11 @@ def measure_single(wl, rank, world, local, steps, warmup, *, e2e=True, r12=True,
     if e2e:
         b_h = b.cpu().pin_memory()
         x_h = torch.zeros_like(b_h).pin_memory()
-        solve(x_h, b_h)
-        e2e_steps = max(1, steps // 2)
+        # warm-up calls like the device timing's: the first host transfer after
+        # a long stretch of device work can run several times slower
+        for _ in range(max(3, warmup)):
+            solve(x_h, b_h)
+        e2e_steps = max(5, steps // 2)
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
@@ -811,9 +814,10 @@ def run_batch(args, rank, world, local, steps=None, sub=False):
         wilson.wilson_solve_batch(hs, xs_h, bs_h, nr, p)
         torch.cuda.synchronize()
 
-    e2e_step()
-    # host copies share the machine's memory system with other jobs: more
-    # steps than the device timing, so that one slow transfer weighs less
+    # warm-up calls like the device timing's: the first host transfer after a
+    # long stretch of device work can run several times slower
+    for _ in range(max(3, args.warmup)):
+        e2e_step()
     e2e_steps = max(5, steps)
     barrier(world)
     t0 = time.perf_counter()
