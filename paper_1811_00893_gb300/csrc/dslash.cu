@@ -203,7 +203,7 @@ static int tuned_shape(wl_gauge g, const HopLaunch& h, int lf, HopArgs& A, int n
         const char* fb = getenv("WL_HOP_BLOCK");
         const int v = fb ? atoi(fb) : 0;
         const int b = v > kFullGrid ? v - kFullGrid : v;
-        if (((b == 64 || b == 128 || b == 256) && (v < kFullGrid || h.dot)) ||
+        if (((b == 32 || b == 64 || b == 128 || b == 256) && (v < kFullGrid || h.dot)) ||
             (v == kRowsShape && rows_allowed(h, lf))) {
             *shape = v;
             return WL_OK;
@@ -232,9 +232,15 @@ static int tuned_shape(wl_gauge g, const HopLaunch& h, int lf, HopArgs& A, int n
             for (int b : {64, 128, 256}) cand.push_back(kPerRhs + b);
         }
     } else {
+        // 32-thread blocks too on small launches, whose grids would otherwise
+        // reach only some of the SMs
+        const bool small = g->geo.Vh * h.nparity <= 65536;
         cand = {64, 128, 256};
-        if (h.dot)
+        if (small) cand.push_back(32);
+        if (h.dot) {
             for (int b : {64, 128, 256}) cand.push_back(kFullGrid + b);
+            if (small) cand.push_back(kFullGrid + 32);
+        }
         if (rows_allowed(h, lf)) cand.push_back(kRowsShape);
     }
     // the timings must not share the GPU with work on other streams (a

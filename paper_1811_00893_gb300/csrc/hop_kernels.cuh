@@ -270,8 +270,10 @@ __global__ void __launch_bounds__(256, 2) hop_mrhs_pipe_kernel(const HopArgs A, 
 // a third of hop_kernel's chain per thread and no exchange between the three.
 // Every output component sees hop_kernel's operations in the same order.
 // Block: kRowSites sites x 3 rows (thread t: row t / kRowSites); a reducing
-// launch leaves one partial per block for the finishing launch.
-static constexpr int kRowSites = 64;
+// launch leaves one partial per block for the finishing launch.  32 sites per
+// block spread an 8^4 lattice's 2 x 2,048 sites over 128 SMs: on small lattices
+// the FP64 pipes of the SMs a launch reaches are its limit.
+static constexpr int kRowSites = 32;
 
 template <int D, int MU, int S>
 __device__ __forceinline__ void hop_row(cx<double> (&acc)[12], const char* in, long long Vh, int nb,

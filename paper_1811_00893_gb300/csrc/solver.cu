@@ -369,16 +369,27 @@ static int apply_A(wl_gauge g, Workspace* w, int prec, void* out, const void* in
     return launch_hop(g, h, s);
 }
 
+// Threads per block of the per-iteration vector kernels over n elements: 256,
+// or fewer on small lattices, so that the grid still reaches every SM (an 8^4
+// FP64 solve's updates are bound by the FP64 pipes of the SMs they run on).
+static int vec_block(long long n, int sms)
+{
+    int b = kBlock;
+    while (b > 32 && (n + b - 1) / b < 2LL * sms) b >>= 1;
+    return b;
+}
+
 static int enqueue_iteration(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
 {
     const int P = w->inner;
     const Vec2 v = vec_of(g, P, w->nhalf);
     const Vec2 vx = vec_of(g, w->xlo_prec, w->nhalf);
-    const dim3 grid((unsigned)((w->nhalf * g->geo.Vh + kBlock - 1) / kBlock), (unsigned)nrhs);
+    const int vb = vec_block(w->nhalf * g->geo.Vh, g->num_sms);
+    const dim3 grid((unsigned)((w->nhalf * g->geo.Vh + vb - 1) / vb), (unsigned)nrhs);
     const int* active = &w->sc[0].active;
     WL_TRY(dispatch_prec(P, [&](auto pc) -> int {
         constexpr int PP = decltype(pc)::value;
-        update_p_kernel<PP><<<grid, kBlock, 0, s>>>((char*)w->p, (const char*)w->r,
+        update_p_kernel<PP><<<grid, vb, 0, s>>>((char*)w->p, (const char*)w->r,
                                                     (const char*)w->v, v, w->sc);
         WL_CHECK_LAUNCH(4.0 * w->vb * nrhs);
         return WL_OK;
@@ -386,7 +397,7 @@ static int enqueue_iteration(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
     WL_TRY(apply_A(g, w, P, w->v, w->p, w->rh, w->sc[0].rv, active, nrhs, s));
     WL_TRY(dispatch_prec(P, [&](auto pc) -> int {
         constexpr int PP = decltype(pc)::value;
-        update_s_kernel<PP><<<grid, kBlock, 0, s>>>((char*)w->s, (const char*)w->r,
+        update_s_kernel<PP><<<grid, vb, 0, s>>>((char*)w->s, (const char*)w->r,
                                                     (const char*)w->v, v, w->sc);
         WL_CHECK_LAUNCH(3.0 * w->vb * nrhs);
         return WL_OK;
@@ -399,13 +410,13 @@ static int enqueue_iteration(wl_gauge g, Workspace* w, int nrhs, cudaStream_t s)
         rgrid.x = std::min(grid.x, (unsigned)resident_grid(
                                        w->xlo_prec == WL_F64 ? (const void*)update_xr_kernel<PP, WL_F64>
                                                              : (const void*)update_xr_kernel<PP, WL_F32>,
-                                       kBlock, 0));
+                                       vb, 0));
         if (w->xlo_prec == WL_F64)
-            update_xr_kernel<PP, WL_F64><<<rgrid, kBlock, 0, s>>>(
+            update_xr_kernel<PP, WL_F64><<<rgrid, vb, 0, s>>>(
                 (char*)w->xlo, vx, (char*)w->r, (const char*)w->p, (const char*)w->s,
                 (const char*)w->t, (const char*)w->rh, v, w->sc, g->red);
         else
-            update_xr_kernel<PP, WL_F32><<<rgrid, kBlock, 0, s>>>(
+            update_xr_kernel<PP, WL_F32><<<rgrid, vb, 0, s>>>(
                 (char*)w->xlo, vx, (char*)w->r, (const char*)w->p, (const char*)w->s,
                 (const char*)w->t, (const char*)w->rh, v, w->sc, g->red);
         // reads p, s, t, rhat and x; writes x and r

@@ -333,11 +333,12 @@ def test_rhs_beyond_one_launch_chunk(prec):
         c.close()
 
 
-@pytest.mark.parametrize("shape", [64, 256, 1064, 1128])
+@pytest.mark.parametrize("shape", [32, 64, 256, 1032, 1064, 1128])
 def test_reducing_hop_shapes_in_solve(monkeypatch, shape):
     """Both forms of the reducing single-RHS hop (grid of resident blocks with
-    a last-block sum; full grid with a finishing launch, shapes 1000 + block)
-    drive a solve to the true residual."""
+    a last-block sum; full grid with a finishing launch, shapes 1000 + block),
+    down to the 32-thread blocks of small lattices, drive a solve to the true
+    residual."""
     monkeypatch.setenv("WL_HOP_BLOCK", str(shape))
     c = Case((6, 2, 2, 6), kappa=0.124, kind="haar", seed=29, bc=(1, 1, 1, -1))
     try:
@@ -386,13 +387,19 @@ def _fp64_ops(monkeypatch, shape, dims, bc):
         raise
 
 
-@pytest.mark.parametrize("dims", [(6, 4, 4, 6), (4, 4, 4, 4)])  # Vh = 288 (ragged), 128
+# Vh = 144 (ragged: 4.5 blocks of 32 sites), 288 and 128
+@pytest.mark.parametrize("dims", [(6, 4, 2, 6), (6, 4, 4, 6), (4, 4, 4, 4)])
 def test_fp64_rows_kernel_equals_one_thread_per_site(monkeypatch, dims):
     """The three-threads-per-site FP64 hop gives the one-thread-per-site
     kernel's result bit for bit (same operations per output component), and
-    both match the oracle."""
+    both match the oracle; so does the one-thread-per-site kernel in 32-thread
+    blocks."""
     bc = (1, 1, 1, -1)
+    c0, _, small = _fp64_ops(monkeypatch, 32, dims, bc)
+    c0.close()
     c1, psi, ref = _fp64_ops(monkeypatch, 128, dims, bc)
+    for (name, p, dagger, a), (_, _, _, b) in zip(ref, small):
+        assert torch.equal(a, b), (name, p, dagger, "32-thread blocks")
     c1.close()
     c2, _, got = _fp64_ops(monkeypatch, 2000, dims, bc)
     try:
