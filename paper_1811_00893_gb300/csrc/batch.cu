@@ -7,12 +7,13 @@
 //   sides) from an atomic counter until the batch is exhausted; each item's
 //   links are staged in shared memory once for all right-hand sides.  Dot
 //   products are written per item and added up, item by item in a fixed
-//   order, by the last block to leave, which also resets the counter.  No
-//   block ever waits for another.
+//   order, by a finishing launch; the last block to leave resets the
+//   counter.  No block ever waits for another.
 // * Vector updates: one launch per update, grid.y = system (lattice, rhs).
 // * FP64 work (residuals, reliable updates, reconstruction) stays per lattice
-//   through the single-lattice path; between its rounds a lattice's systems
-//   are inactive and the batched kernels skip them.
+//   through the single-lattice path, on the lattice's own stream, so that
+//   the lattices' steps run side by side; between its rounds a lattice's
+//   systems are inactive and the batched kernels skip them.
 #include <algorithm>
 #include <cstring>
 #include <memory>
