@@ -73,6 +73,7 @@ struct Workspace {
     bool graph_timed = false;   // captured while per-launch timing was on
     size_t graph_tslots = 0;    // its timed launches (capture slots)
     cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+    int tuned_nrhs = 0;  // the iteration's hopping launches were timed for this many rhs
     // the solution's canonical copy (and host copy) while the final check runs
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_x = nullptr, ev_sent = nullptr;
